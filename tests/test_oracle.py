@@ -1,0 +1,493 @@
+"""Pins of the oracle against facts that do not come from the oracle itself:
+a hand-derived worked example, closed forms, brute force on tiny grids, the
+theorems' batch forms, invariants and finite differences (CPU only)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_12945_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+V, TAU = 0.1, 0.3
+
+
+def _pose_t(x, y, z):
+    m = np.eye(4)
+    m[:3, 3] = (x, y, z)
+    return m
+
+
+def _rand_pose(rng, spread=0.3):
+    a = rng.uniform(0, 2 * math.pi, 3)
+    cx, sx = math.cos(a[0]), math.sin(a[0])
+    cy, sy = math.cos(a[1]), math.sin(a[1])
+    cz, sz = math.cos(a[2]), math.sin(a[2])
+    Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+    Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+    m = np.eye(4)
+    m[:3, :3] = Rz @ Ry @ Rx
+    m[:3, 3] = rng.uniform(-spread, spread, 3)
+    return m
+
+
+def _onehot_probs(labels, K):
+    p = np.full((len(labels), K), 0.05, np.float32)
+    p[np.arange(len(labels)), labels] = 0.6
+    return p
+
+
+# ------------------------------------------------------------- worked example
+def _golden_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "axis_two_scans.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(x) for x in line.split()])
+    return np.array(rows)
+
+
+def test_worked_example_closed():
+    g = _golden_rows()
+    m = oracle.OracleMap(voxel_size=V, trunc=TAU, num_classes=4, alpha0=1.0)
+    o = _pose_t(0.05, 0.05, 0.05)
+    m.integrate([[1.02, 0, 0]], o, _onehot_probs(np.array([1]), 4))
+    m.integrate([[1.04, 0, 0]], o, _onehot_probs(np.array([2]), 4))
+    e = m.extract()
+    assert np.array_equal(e["ijk"], g[:, :3].astype(np.int32))
+    assert np.array_equal(e["W"], g[:, 3])
+    np.testing.assert_allclose(e["D"], g[:, 4], atol=1e-6)
+    assert np.array_equal(e["sem"], np.tile([0.0, 1.0, 1.0, 0.0], (7, 1)))
+    post = m.extract(posterior=True)["sem"]
+    np.testing.assert_allclose(post, np.tile([1 / 6, 2 / 6, 2 / 6, 1 / 6], (7, 1)), rtol=1e-15)
+
+
+def test_worked_example_open():
+    g = _golden_rows()
+    m = oracle.OracleMap(voxel_size=V, trunc=TAU, mode=oracle.OPEN, embed_dim=2)
+    o = _pose_t(0.05, 0.05, 0.05)
+    m.integrate([[1.02, 0, 0]], o, [[1.0, 0.0]])
+    m.integrate([[1.04, 0, 0]], o, [[0.0, 1.0]])
+    e = m.extract()
+    assert np.array_equal(e["ijk"], g[:, :3].astype(np.int32))
+    np.testing.assert_allclose(e["D"], g[:, 4], atol=1e-6)
+    np.testing.assert_allclose(e["sem"], 0.5, rtol=1e-15)
+    np.testing.assert_allclose(e["beta"], 0.25, rtol=1e-15)
+
+
+def test_worked_example_query():
+    # two orthogonal queries, voxel mean (0.8, 0.6): cosines (0.8, 0.6),
+    # softmax of cos / 0.1 -> p0 = 1 / (1 + e^-2)
+    label, prob, cos = oracle.query(np.array([[0.8, 0.6], [0.0, 0.0]]),
+                                    np.array([[1, 0], [0, 1]], np.float32), 0.1, 0.1)
+    assert label.tolist() == [0, -1]
+    assert prob[0] == pytest.approx(1.0 / (1.0 + math.exp(-2.0)), rel=1e-14)
+    assert prob[1] == 0.0
+    np.testing.assert_allclose(cos[0], [0.8, 0.6], rtol=1e-14)
+    # threshold: 256 equal cosines give p = 1/256 < 0.1 -> rejected
+    q = np.tile(np.array([[1.0, 0.0]], np.float32), (256, 1))
+    label, prob, _ = oracle.query(np.array([[3.0, 0.0]]), q, 0.01, 0.1)
+    assert label[0] == -1 and prob[0] == pytest.approx(1 / 256)
+
+
+# --------------------------------------------------------------- geometry pins
+def test_axis_ray_closed_form():
+    """A ray along +x: the voxels are the x-run covering the band and
+    d = x_0 - c exactly (FP32 rounding only)."""
+    p = oracle.make_params(V, TAU)
+    o = _pose_t(0.05, 0.05, 0.05)
+    for r in [0.517, 1.3337, 2.71, 7.77, 12.345]:
+        vis = oracle.point_visits(p, [r, 0, 0], o)
+        x0 = 0.05 + r
+        lo = math.floor((x0 - TAU) / V)
+        hi = math.floor((x0 + TAU) / V)
+        assert vis[:, 0].tolist() == list(range(lo, hi + 1))
+        assert (vis[:, 1:] == 0).all()
+        ijk, pt, d = oracle.scan_pairs(p, np.array([[r, 0, 0]]), o)
+        c = (ijk[:, 0] + 0.5) * V
+        ref = np.minimum(x0 - c, TAU)
+        keep = (x0 - (np.arange(lo, hi + 1) + 0.5) * V) >= -TAU
+        assert len(d) == keep.sum()
+        np.testing.assert_allclose(d, ref, atol=2e-6)
+
+
+def _segment_cells_fp64(o, x, tau, v, margin):
+    """Cells whose box meets the segment o + t u, t in [max(0, r - tau), r + tau],
+    by brute force over the segment's bounding box. Returns (set, ambiguous)."""
+    dl = x - o
+    r = np.linalg.norm(dl)
+    u = dl / r
+    t0, t1 = max(0.0, r - tau), r + tau
+    a, b = o + t0 * u, o + t1 * u
+    lo = np.floor(np.minimum(a, b) / v).astype(int) - 1
+    hi = np.floor(np.maximum(a, b) / v).astype(int) + 1
+    cells, amb = set(), False
+    for i in range(lo[0], hi[0] + 1):
+        for j in range(lo[1], hi[1] + 1):
+            for k in range(lo[2], hi[2] + 1):
+                cmin = np.array([i, j, k]) * v
+                cmax = cmin + v
+                tin, tout = t0, t1
+                for ax in range(3):
+                    if abs(u[ax]) < 1e-300:
+                        if not (cmin[ax] <= o[ax] < cmax[ax]):
+                            tin, tout = 1.0, 0.0
+                        continue
+                    ta = (cmin[ax] - o[ax]) / u[ax]
+                    tb = (cmax[ax] - o[ax]) / u[ax]
+                    tin = max(tin, min(ta, tb))
+                    tout = min(tout, max(ta, tb))
+                if abs(tout - tin) < margin:
+                    amb = True
+                if tout - tin > 0:
+                    cells.add((i, j, k))
+    return cells, amb
+
+
+def test_dda_brute_force_tiny_grid():
+    """The band DDA enters exactly the cells the band segment meets (seeded
+    random rays in a < 16^3 grid; rays with a near-grazing cell are skipped)."""
+    rng = np.random.default_rng(7)
+    p = oracle.make_params(V, TAU)
+    checked = 0
+    for _ in range(400):
+        pose = _rand_pose(rng, 0.4)
+        pt = rng.uniform(-0.6, 0.6, 3).astype(np.float32)
+        if np.linalg.norm(pt) < 0.05:
+            continue
+        vis = oracle.point_visits(p, pt, pose)
+        assert vis is not None
+        x = pose[:3, :3] @ pt.astype(np.float64) + pose[:3, 3]
+        cells, amb = _segment_cells_fp64(pose[:3, 3], x, TAU, V, 1e-5)
+        if amb:
+            continue
+        got = [tuple(c) for c in vis.tolist()]
+        assert len(set(got)) == len(got), "a voxel was entered twice"
+        assert set(got) == cells
+        # consecutive voxels are face neighbours
+        assert (np.abs(np.diff(vis, axis=0)).sum(axis=1) == 1).all()
+        checked += 1
+    assert checked > 300
+
+
+def test_pair_sdf_and_filter():
+    """Kept pairs have d = (x - c) . u (to FP32 rounding) clamped to tau; the
+    dropped visits are exactly those with d < -tau."""
+    rng = np.random.default_rng(11)
+    p = oracle.make_params(V, TAU)
+    for _ in range(100):
+        pose = _rand_pose(rng, 2.0)
+        pt = rng.uniform(-4, 4, 3).astype(np.float32)
+        vis = oracle.point_visits(p, pt, pose)
+        x = pose[:3, :3] @ pt.astype(np.float64) + pose[:3, 3]
+        u = (x - pose[:3, 3]) / np.linalg.norm(x - pose[:3, 3])
+        dref = ((x[None, :] - (vis + 0.5) * V) * u[None, :]).sum(axis=1)
+        ijk, _, d = oracle.scan_pairs(p, pt[None, :], pose)
+        clear = np.abs(dref + TAU) > 1e-5
+        kept = dref >= -TAU
+        assert len(d) == kept.sum() or not clear.all()
+        if clear.all():
+            assert np.array_equal(ijk, vis[kept])
+            np.testing.assert_allclose(d, np.minimum(dref[kept], TAU), atol=5e-6)
+            assert (d <= np.float32(TAU)).all() and (d >= -np.float32(TAU)).all()
+
+
+def test_invalid_points():
+    p = oracle.make_params(V, TAU, min_range=1.0, max_range=10.0)
+    o = np.eye(4)
+    for bad in [[0.5, 0, 0], [11, 0, 0], [np.nan, 1, 1], [np.inf, 0, 0], [0, 0, 0]]:
+        assert oracle.point_visits(p, bad, o) is None
+    m = oracle.OracleMap(voxel_size=V, trunc=TAU, num_classes=3, min_range=1.0, max_range=10.0)
+    assert m.integrate(np.zeros((0, 3)), o, np.zeros((0, 3))) == 0
+    assert m.integrate([[0.5, 0, 0], [np.nan, 0, 0]], o, np.ones((2, 3))) == 0
+    assert m.count() == 0
+
+
+def test_fp32_vs_fp64_geometry_close():
+    """The FP32 operation order stays within rounding of the FP64 geometry:
+    almost all voxels agree and the shared voxels' D agree to ~1e-6."""
+    w = synth.room_lidar(n_scans=2, n_beams=8, n_az=128)
+    res = []
+    for f64 in (False, True):
+        m = oracle.OracleMap(voxel_size=V, trunc=TAU, num_classes=10, min_range=0.1,
+                             max_range=100.0, fp64_geometry=f64)
+        for s in w.scans:
+            m.integrate(s["pts"], s["pose"], s["sem"])
+        res.append(m.extract())
+    a, b = res
+    ka = {tuple(k) for k in a["ijk"].tolist()}
+    kb = {tuple(k) for k in b["ijk"].tolist()}
+    assert len(ka ^ kb) <= 1e-3 * len(ka)
+
+
+# ----------------------------------------------------------------- fusion pins
+def _groupby_pairs(params, scans):
+    """Per-voxel observation lists from the oracle's pair generator."""
+    obs = {}
+    for si, s in enumerate(scans):
+        ijk, pt, d = oracle.scan_pairs(params, s["pts"], s["pose"])
+        for k in range(len(d)):
+            obs.setdefault(tuple(ijk[k]), []).append((si, int(pt[k]), d[k]))
+    return obs
+
+
+def test_tsdf_counts_closed_forms():
+    """W = number of observations, D = their mean (w~ = 1), one-hot counts =
+    per-class observation counts (Theorem 1), sum c = W, posterior sums to 1."""
+    w = synth.room_lidar(n_scans=3, n_beams=8, n_az=96)
+    m = oracle.OracleMap(voxel_size=V, trunc=TAU, num_classes=10, min_range=0.1, max_range=100.0)
+    for s in w.scans:
+        m.integrate(s["pts"], s["pose"], s["sem"])
+    e = m.extract()
+    obs = _groupby_pairs(m.params, w.scans)
+    assert len(obs) == len(e["W"])
+    for k, key in enumerate(map(tuple, e["ijk"].tolist())):
+        lst = obs[key]
+        assert e["W"][k] == len(lst)
+        assert e["D"][k] == pytest.approx(np.mean([x[2] for x in lst]), rel=1e-12, abs=1e-15)
+        cnt = np.zeros(10)
+        for si, j, _ in lst:
+            cnt[int(np.argmax(w.scans[si]["sem"][j]))] += 1
+        assert np.array_equal(e["sem"][k], cnt)
+    assert np.array_equal(e["sem"].sum(axis=1), e["W"])
+    post = m.extract(posterior=True)["sem"]
+    np.testing.assert_allclose(post.sum(axis=1), 1.0, rtol=1e-14)
+
+
+def test_posterior_single_class_and_alpha0():
+    o = _pose_t(0.05, 0.05, 0.05)
+    for a0 in (0.0, 1.0, 2.5):
+        m = oracle.OracleMap(voxel_size=V, trunc=TAU, num_classes=5, alpha0=a0)
+        for r in (1.02, 1.03, 1.04):
+            m.integrate([[r, 0, 0]], o, _onehot_probs(np.array([3]), 5))
+        e = m.extract(posterior=True)
+        W = m.extract()["W"]
+        for k in range(len(W)):
+            exp = np.full(5, a0 / (5 * a0 + W[k]))
+            exp[3] = (a0 + W[k]) / (5 * a0 + W[k])
+            np.testing.assert_allclose(e["sem"][k], exp, rtol=1e-15)
+
+
+def test_order_and_split_independence():
+    """Theorems 1-2 hold for observation sets: scan order and any split of a
+    scan into several calls give the same posterior (to FP64 rounding)."""
+    w = synth.room_lidar(n_scans=3, n_beams=8, n_az=64)
+    for mode, K, L in ((oracle.CLOSED_ONEHOT, 10, 0), (oracle.CLOSED_SOFT, 10, 0)):
+        outs = []
+        for order in ([0, 1, 2], [2, 0, 1], "split"):
+            m = oracle.OracleMap(voxel_size=V, trunc=TAU, mode=mode, num_classes=K,
+                                 min_range=0.1, max_range=100.0)
+            if order == "split":
+                for s in w.scans[::-1]:
+                    h = s["pts"].shape[0] // 3
+                    m.integrate(s["pts"][h:], s["pose"], s["sem"][h:])
+                    m.integrate(s["pts"][:h], s["pose"], s["sem"][:h])
+            else:
+                for i in order:
+                    m.integrate(w.scans[i]["pts"], w.scans[i]["pose"], w.scans[i]["sem"])
+            outs.append(m.extract())
+        for o in outs[1:]:
+            assert np.array_equal(o["ijk"], outs[0]["ijk"])
+            assert np.array_equal(o["W"], outs[0]["W"])
+            np.testing.assert_allclose(o["D"], outs[0]["D"], rtol=1e-12, atol=1e-15)
+            np.testing.assert_allclose(o["sem"], outs[0]["sem"], rtol=1e-12, atol=1e-13)
+
+
+def _open_scans(n_scans=3, dim=6, seed=5):
+    w = synth.indoor_rgbd(seed=seed, n_frames=40, width=24, height=18, dim=dim,
+                          frames=list(range(n_scans)))
+    return w
+
+
+def test_open_set_theorem2_batch_form():
+    """The oracle's one-observation recursion equals Theorem 2 applied once per
+    scan to that scan's observation set (Eqs. norm_update_1-4), with lambda
+    and nu tracked separately from zero priors; lambda = 2 nu = W holds."""
+    w = _open_scans()
+    m = oracle.OracleMap(voxel_size=0.05, trunc=0.15, mode=oracle.OPEN, embed_dim=6,
+                         min_range=0.3, max_range=8.0)
+    for s in w.scans:
+        m.integrate(s["pts"], s["pose"], s["sem"])
+    e = m.extract()
+    state = {}
+    for s in w.scans:
+        ijk, pt, _ = oracle.scan_pairs(m.params, s["pts"], s["pose"])
+        per = {}
+        for k in range(len(pt)):
+            per.setdefault(tuple(ijk[k]), []).append(s["sem"][pt[k]].astype(np.float64))
+        for key, zs in per.items():
+            Z = np.array(zs)
+            n = Z.shape[0]
+            zbar = Z.mean(axis=0)
+            mm, lam, nu, beta = state.get(key, (np.zeros(6), 0.0, 0.0, np.zeros(6)))
+            lam_t = lam + n
+            m_t = (lam * mm + n * zbar) / lam_t
+            nu_t = nu + n / 2.0
+            beta_t = beta + 0.5 * ((Z - zbar) ** 2).sum(axis=0) + \
+                (lam * n / lam_t) * (zbar - mm) ** 2 / 2.0
+            state[key] = (m_t, lam_t, nu_t, beta_t)
+    assert len(state) == len(e["W"])
+    for k, key in enumerate(map(tuple, e["ijk"].tolist())):
+        m_t, lam_t, nu_t, beta_t = state[key]
+        assert lam_t == e["W"][k] and 2 * nu_t == e["W"][k]
+        np.testing.assert_allclose(e["sem"][k], m_t, rtol=1e-10, atol=1e-14)
+        np.testing.assert_allclose(e["beta"][k], beta_t, rtol=1e-9, atol=1e-14)
+
+
+def test_open_set_textbook_and_identical():
+    """Zero priors: m = sample mean, beta = 1/2 sum of squared deviations;
+    identical observations give m = z and beta = 0."""
+    w = _open_scans(n_scans=2)
+    m = oracle.OracleMap(voxel_size=0.05, trunc=0.15, mode=oracle.OPEN, embed_dim=6,
+                         min_range=0.3, max_range=8.0)
+    for s in w.scans:
+        m.integrate(s["pts"], s["pose"], s["sem"])
+    e = m.extract()
+    per = {}
+    for s in w.scans:
+        ijk, pt, _ = oracle.scan_pairs(m.params, s["pts"], s["pose"])
+        for k in range(len(pt)):
+            per.setdefault(tuple(ijk[k]), []).append(s["sem"][pt[k]].astype(np.float64))
+    for k, key in enumerate(map(tuple, e["ijk"].tolist())):
+        Z = np.array(per[key])
+        np.testing.assert_allclose(e["sem"][k], Z.mean(axis=0), rtol=1e-10, atol=1e-14)
+        np.testing.assert_allclose(e["beta"][k], 0.5 * ((Z - Z.mean(0)) ** 2).sum(0),
+                                   rtol=1e-9, atol=1e-14)
+    z = np.array([0.3, -0.2, 0.5, 0.1, 0.0, 0.7], np.float32)
+    m2 = oracle.OracleMap(voxel_size=0.05, trunc=0.15, mode=oracle.OPEN, embed_dim=6,
+                          min_range=0.3, max_range=8.0)
+    for s in w.scans:
+        m2.integrate(s["pts"], s["pose"], np.tile(z, (s["pts"].shape[0], 1)))
+    e2 = m2.extract()
+    np.testing.assert_allclose(e2["sem"], np.tile(z.astype(np.float64), (len(e2["W"]), 1)),
+                               rtol=1e-14)
+    assert np.abs(e2["beta"]).max() < 1e-14
+
+
+def test_extract_order():
+    w = synth.room_lidar(n_scans=1, n_beams=8, n_az=64)
+    m = oracle.OracleMap(voxel_size=V, trunc=TAU, num_classes=10, min_range=0.1, max_range=100.0)
+    m.integrate(w.scans[0]["pts"], w.scans[0]["pose"], w.scans[0]["sem"])
+    ijk = m.extract()["ijk"].astype(np.int64)
+    b = np.floor_divide(ijk, 8)
+    loc = ((ijk[:, 0] - 8 * b[:, 0]) * 8 + (ijk[:, 1] - 8 * b[:, 1])) * 8 + (ijk[:, 2] - 8 * b[:, 2])
+    keys = list(zip(b[:, 0], b[:, 1], b[:, 2], loc))
+    assert keys == sorted(keys) and len(set(keys)) == len(keys)
+
+
+def test_query_brute_force():
+    rng = np.random.default_rng(3)
+    rows = rng.standard_normal((50, 16))
+    rows[7] = 0.0
+    q = synth.random_queries(4, 32, 16)
+    label, prob, cos = oracle.query(rows, q, 0.05, 0.1)
+    q64 = q.astype(np.float64)
+    c = (rows @ q64.T) / np.maximum(
+        np.linalg.norm(rows, axis=1, keepdims=True), 1e-300) / np.linalg.norm(q64, axis=1)[None]
+    best = np.argmax(c, axis=1)
+    e = np.exp((c - c.max(1, keepdims=True)) / 0.05)
+    pb = e.max(1) / e.sum(1)
+    for i in range(50):
+        if i == 7:
+            assert label[i] == -1 and prob[i] == 0
+            continue
+        assert prob[i] == pytest.approx(pb[i], rel=1e-12)
+        assert label[i] == (best[i] if pb[i] >= 0.1 else -1)
+        np.testing.assert_allclose(cos[i], c[i], rtol=1e-12, atol=1e-14)
+
+
+# -------------------------------------------------------------- gradient pins
+def _fd_map(params_kw, scans):
+    m = oracle.OracleMap(**params_kw)
+    for s in scans:
+        m.integrate(s["pts"], s["pose"], s["sem"])
+    return m
+
+
+def test_backward_closed_soft_fd():
+    """The oracle's adjoint matches central finite differences of its own
+    FP64-geometry forward pass (pair sets held fixed by choice of h)."""
+    rng = np.random.default_rng(12)
+    w = synth.room_lidar(n_scans=2, n_beams=6, n_az=40, K=5, mode="soft")
+    kw = dict(voxel_size=V, trunc=TAU, mode=oracle.CLOSED_SOFT, num_classes=5,
+              min_range=0.1, max_range=100.0, alpha0=1.0)
+    base = _fd_map(kw, w.scans)
+    e = base.extract()
+    nv = len(e["W"])
+    a = rng.standard_normal(nv)
+    B = rng.standard_normal((nv, 5))
+    keys = e["ijk"]
+
+    def loss(ext):
+        assert np.array_equal(ext["ijk"], keys)
+        c = ext["sem"]
+        post = (1.0 + c) / (5.0 + c.sum(1, keepdims=True))
+        return float((a * ext["D"] ** 2).sum() + (B * np.log(post)).sum())
+
+    c = e["sem"]
+    tot = 5.0 + c.sum(1, keepdims=True)
+    gD = 2 * a * e["D"]
+    gS = B / (1.0 + c) - B.sum(1, keepdims=True) / tot
+    s0 = w.scans[0]
+    gsem, gxyz = base.backward_scan(s0["pts"], s0["pose"], s0["sem"], gD, gS)
+    kw64 = dict(kw, fp64_geometry=True)
+    idx = rng.choice(np.flatnonzero(np.linalg.norm(s0["pts"], axis=1) > 0.1), 6, replace=False)
+    for j in idx:
+        for comp in range(3):
+            h = 1e-4
+            vals = []
+            for sgn in (1, -1):
+                sc = [dict(s) for s in w.scans]
+                pts = s0["pts"].astype(np.float64).copy()
+                pts[j, comp] += sgn * h
+                sc[0]["pts"] = pts.astype(np.float32)
+                # the perturbation is applied in float32; use the realised step
+                vals.append((loss(_fd_map(kw64, sc).extract()), float(sc[0]["pts"][j, comp])))
+            fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+            assert gxyz[j, comp] == pytest.approx(fd, rel=2e-3, abs=2e-3)
+        for k in range(5):
+            h = 1e-3
+            vals = []
+            for sgn in (1, -1):
+                sc = [dict(s) for s in w.scans]
+                sem = s0["sem"].astype(np.float64).copy()
+                sem[j, k] += sgn * h
+                sc[0]["sem"] = sem.astype(np.float32)
+                vals.append((loss(_fd_map(kw, sc).extract()), float(sc[0]["sem"][j, k])))
+            fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+            assert gsem[j, k] == pytest.approx(fd, rel=1e-3, abs=1e-5)
+
+
+def test_backward_open_fd():
+    rng = np.random.default_rng(13)
+    w = _open_scans(n_scans=2, dim=4, seed=9)
+    kw = dict(voxel_size=0.05, trunc=0.15, mode=oracle.OPEN, embed_dim=4,
+              min_range=0.3, max_range=8.0)
+    base = _fd_map(kw, w.scans)
+    e = base.extract()
+    nv = len(e["W"])
+    A = rng.standard_normal((nv, 4))
+    Bq = rng.standard_normal((nv, 4))
+
+    def loss(ext):
+        return float((A * ext["sem"] ** 2).sum() + (Bq * ext["beta"]).sum())
+
+    gS = 2 * A * e["sem"]
+    s1 = w.scans[1]
+    gsem, _ = base.backward_scan(s1["pts"], s1["pose"], s1["sem"], np.zeros(nv), gS, Bq)
+    idx = rng.choice(np.flatnonzero(np.linalg.norm(s1["pts"], axis=1) > 0.3), 5, replace=False)
+    for j in idx:
+        for k in range(4):
+            h = 1e-3
+            vals = []
+            for sgn in (1, -1):
+                sc = [dict(s) for s in w.scans]
+                sem = s1["sem"].astype(np.float64).copy()
+                sem[j, k] += sgn * h
+                sc[1]["sem"] = sem.astype(np.float32)
+                vals.append((loss(_fd_map(kw, sc).extract()), float(sc[1]["sem"][j, k])))
+            fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+            assert gsem[j, k] == pytest.approx(fd, rel=1e-3, abs=1e-6)
