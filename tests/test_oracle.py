@@ -491,3 +491,18 @@ def test_backward_open_fd():
                 vals.append((loss(_fd_map(kw, sc).extract()), float(sc[1]["sem"][j, k])))
             fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
             assert gsem[j, k] == pytest.approx(fd, rel=1e-3, abs=1e-6)
+
+
+def test_dda_tie_breaks_to_lowest_axis():
+    """On exact ties of the next crossing the DDA steps the lowest axis first
+    (x, then y, then z): a (1,1,1) ray from a voxel centre crosses all three
+    planes at the same t, so the visits cycle x, y, z."""
+    p = oracle.make_params(V, TAU)
+    o = _pose_t(0.05, 0.05, 0.05)
+    for a in (0.7, 1.9):
+        vis = oracle.point_visits(p, [a, a, a], o)
+        steps = np.diff(vis, axis=0)
+        axes = [int(np.flatnonzero(s)[0]) for s in steps]
+        assert (np.abs(steps).sum(axis=1) == 1).all()
+        assert len(axes) >= 4
+        assert axes == [0, 1, 2] * (len(axes) // 3) + [0, 1, 2][:len(axes) % 3]
