@@ -1,0 +1,215 @@
+/*
+ * slim_gb300.h — C ABI of the GB300 scan-integration library for SLIM-VDB
+ * style probabilistic semantic TSDF maps (arXiv 2512.12945).
+ *
+ * The library keeps one sparse voxel map per slim_map handle on one CUDA
+ * device: 8^3-voxel blocks behind an open-addressing hash, each voxel holding
+ * a truncated signed distance D, a weight W and its semantic state — Dirichlet
+ * class counts (closed set, Sec. III-C) or the Normal-Inverse-Gamma mean m
+ * and diagonal beta of an l-dimensional embedding (open set, Sec. III-D).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are CUDA device memory owned by the caller; the
+ *     library never frees them and never keeps them after the call returns
+ *     (work it queued on `stream` may still read them until the stream
+ *     reaches that point). Pointers named *_host are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Work is queued asynchronously on it unless stated otherwise.
+ *   - Arguments are checked on the host before anything is queued; a bad
+ *     argument returns SLIM_ERR_ARG and queues nothing.
+ *   - Faults found on the device (capacity exhausted, a bounded probe or wait
+ *     that ran out) set a sticky status word in the map. Kernels of a scan
+ *     that sees a non-zero status leave the voxel fields untouched. The status
+ *     is returned by slim_map_sync and by the next call that synchronises;
+ *     slim_map_reset clears it.
+ *   - No exception or longjmp crosses this boundary. A map handle must not be
+ *     used from two host threads at once.
+ *   - slim_last_error() gives a human-readable message for the last failure
+ *     on the calling thread.
+ */
+#ifndef SLIM_GB300_H
+#define SLIM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SLIM_OK = 0,
+  SLIM_ERR_ARG = 1,         /* invalid argument (nothing queued) */
+  SLIM_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  SLIM_ERR_CAPACITY = 3,    /* block, voxel, hash or scratch capacity exhausted */
+  SLIM_ERR_TIMEOUT = 4,     /* a bounded device-side probe or wait ran out */
+  SLIM_ERR_NOMEM = 5,       /* device allocation failed at map creation */
+  SLIM_ERR_UNSUPPORTED = 6, /* valid request this map's mode cannot serve */
+  SLIM_ERR_INTERNAL = 7     /* an internal device-side consistency check failed */
+} slim_status;
+
+/* Semantic fusion mode. */
+typedef enum {
+  /* Theorem 1 / Eq. (alpha_update): each observation adds 1 to the count of
+   * its most probable class (argmax of the per-point probabilities, ties to
+   * the lowest index). */
+  SLIM_CLOSED_ONEHOT = 0,
+  /* Soft-count reading of Eq. (alpha_update): each observation adds its whole
+   * probability vector (the mode the adjoint differentiates). */
+  SLIM_CLOSED_SOFT = 1,
+  /* Theorem 2 / Eqs. (norm_update_1)-(norm_update_4) with lambda = 2 nu = W
+   * (Sec. III-D): per-element NIG mean m and beta of l-dim embeddings. */
+  SLIM_OPEN = 2
+} slim_mode;
+
+typedef enum { SLIM_STORE_F32 = 0, SLIM_STORE_BF16 = 1 } slim_storage;
+
+typedef struct {
+  float voxel_size;      /* metres, > 0 */
+  float trunc;           /* truncation tau in metres, 0 < tau <= 4 voxel_size */
+  float min_range;       /* valid sensor-frame range [min_range, max_range] */
+  float max_range;
+  int32_t mode;          /* slim_mode */
+  int32_t num_classes;   /* K for the closed-set modes (1..64) */
+  int32_t embed_dim;     /* l for SLIM_OPEN (multiple of 64, 64..1024) */
+  int32_t embed_storage; /* slim_storage of m and beta (SLIM_OPEN) */
+  double alpha0;         /* Dirichlet prior per class, >= 0 (read-out only) */
+  double body_from_sensor[16]; /* row-major 4x4 extrinsic, FP64 */
+  int64_t block_capacity;  /* maximum allocated 8^3 blocks */
+  int64_t hash_capacity;   /* hash entries (rounded up to 32 x power of 2) */
+  int64_t voxel_capacity;  /* SLIM_OPEN: maximum allocated voxels */
+  int64_t max_points;      /* largest scan passed to slim_integrate */
+} slim_map_params;
+
+typedef struct slim_map slim_map;
+
+typedef struct {
+  int64_t blocks;        /* allocated blocks */
+  int64_t voxels;        /* SLIM_OPEN: allocated voxel rows; closed: -1 */
+  int64_t device_bytes;  /* device memory held by the map */
+  int64_t scans;         /* scans integrated since creation / reset */
+  uint32_t status;       /* sticky device status (slim_status value) */
+} slim_stats;
+
+/* Fill *p with defaults: 0.1 m voxels, tau = 0.3 m, closed one-hot with
+ * K = 20, alpha0 = 1, identity extrinsic, capacities for ~1e5 blocks. */
+slim_status slim_map_params_default(slim_map_params* p);
+
+/* Create a map on the current CUDA device. The map allocates and owns its
+ * hash, block pool, voxel storage and scratch (cudaMalloc, synchronous).
+ * *out receives the handle. */
+slim_status slim_map_create(const slim_map_params* p, slim_map** out);
+
+/* Release everything the map owns (synchronises the device first). */
+slim_status slim_map_destroy(slim_map* m);
+
+/* Empty the map (all blocks and voxels gone, status cleared), keeping its
+ * memory. Queued on `stream`. */
+slim_status slim_map_reset(slim_map* m, void* stream);
+
+/* Integrate one scan (Sec. III-A to III-D). For each of the n points:
+ *   p = pts_dev[3j .. 3j+2], the sensor-frame point (float32, AoS xyz);
+ *   valid iff finite, min_range <= |p| <= max_range and within 2^19 voxels
+ *   of the world origin; world point x = R p + t with
+ *   [R t] = pose_host (row-major 4x4 world_from_body, FP64) composed with
+ *   body_from_sensor in FP64 on the host, then rounded once to float32.
+ *   The ray from o = t through x is marched over the band
+ *   t in [max(0, r - tau), r + tau] (Amanatides & Woo); each voxel entered
+ *   with along-ray SDF d = (x - c) . u >= -tau receives one observation
+ *   min(d, tau) and the point's semantics:
+ *     closed modes: sem_dev = n x K float32 class probabilities (row-major);
+ *     SLIM_OPEN:    sem_dev = n x l float32 embeddings (row-major).
+ * Fusion: W += 1, D running average (w~ = 1), then the mode's update.
+ * n may be 0. n <= max_points. Asynchronous on `stream`. */
+slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
+                           const double pose_host[16], const void* sem_dev,
+                           void* stream);
+
+/* As slim_integrate with pts_host / sem_host in host memory: the library
+ * copies them into its own device staging buffers on `stream` (pinned host
+ * memory makes the copies asynchronous). The host buffers must stay valid
+ * until the stream reaches the copies. */
+slim_status slim_integrate_host(slim_map* m, const float* pts_host, int64_t n,
+                                const double pose_host[16], const void* sem_host,
+                                void* stream);
+
+/* Wait for `stream` and return the map's sticky device status. */
+slim_status slim_map_sync(slim_map* m, void* stream);
+
+/* Host-side counters (synchronises `stream` to read device counters). */
+slim_status slim_map_stats(slim_map* m, slim_stats* out, void* stream);
+
+/* Extract flags. */
+#define SLIM_EXTRACT_POSTERIOR 1 /* closed set: sem = Eq. (dir_to_cat)
+                                    posterior (alpha0 + c_i)/(K alpha0 + sum c)
+                                    instead of the raw counts c */
+
+/* Export every allocated voxel (W > 0), ordered by block coordinates
+ * (bx, by, bz) lexicographically, then by the local index
+ * ((ix & 7) * 8 + (iy & 7)) * 8 + (iz & 7).
+ * Two-call protocol: with cap == 0 only *n_out is written (the call
+ * synchronises `stream`). With cap >= *n_out the outputs are written:
+ *   ijk_dev   n x 3 int32 voxel indices (may be NULL)
+ *   D_dev, W_dev  n float32 (may be NULL)
+ *   sem_dev   closed: n x K float32 counts or posteriors; open: n x l float32
+ *             NIG means m (may be NULL)
+ *   beta_dev  open: n x l float32 NIG beta (may be NULL; ignored if closed)
+ *   index_dev n int32 internal voxel index (closed: slot*512 + local; open:
+ *             voxel row) as used by slim_backward (may be NULL).
+ * The call synchronises `stream`. cap < *n_out returns SLIM_ERR_CAPACITY. */
+slim_status slim_extract_tsdf(slim_map* m, int32_t* ijk_dev, float* D_dev, float* W_dev,
+                              float* sem_dev, float* beta_dev, int32_t* index_dev,
+                              int64_t cap, int64_t* n_out, int32_t flags, void* stream);
+
+/* Open-set read-out (end of Sec. III-D; Fig. "sit"): for every voxel row v
+ * (0 .. voxels-1), cosine similarity s_vq = m_v . q_q / (|m_v| |q_q|) against
+ * q queries (q_dev: q x l, bf16 bit patterns, row-major), softmax over the
+ * queries of s / temperature, label_dev[v] = most probable query (ties to
+ * the lowest index) if its probability >= tp, else -1; prob_dev[v] = that
+ * probability. Rows with |m| = 0 get label -1, prob 0. scores_dev (voxels x q
+ * float32 cosine similarities) may be NULL. The contraction runs on the
+ * tcgen05 tensor cores in BF16 with FP32 accumulation. 1 <= q <= 256. */
+slim_status slim_query(slim_map* m, const uint16_t* q_dev, int32_t q, float temperature,
+                       float tp, int32_t* label_dev, float* prob_dev, float* scores_dev,
+                       void* stream);
+
+/* Reverse mode of a map integrated from empty (zero priors, so the state is
+ * the batch posterior of all observations, Theorems 1-2). Given loss
+ * gradients per voxel (indexed like index_dev of slim_extract_tsdf, arrays
+ * sized to cover the largest index + 1):
+ *   gD_dev  dL/dD          (float32)
+ *   gS_dev  closed SOFT: dL/dc (x K); open: dL/dm (x l)       (float32)
+ *   gB_dev  open: dL/dbeta (x l) or NULL
+ * writes, for one scan's n points (the same pts_dev, pose_host and sem_dev
+ * that were integrated), gsem_dev = dL/dsem (n x K or n x l) and
+ * gxyz_dev = dL/dp (n x 3, sensor frame); invalid points get zeros.
+ * The (voxel, point) pairs are recomputed, not stored. */
+slim_status slim_backward(slim_map* m, const float* pts_dev, int64_t n,
+                          const double pose_host[16], const void* sem_dev,
+                          const float* gD_dev, const float* gS_dev, const float* gB_dev,
+                          float* gsem_dev, float* gxyz_dev, void* stream);
+
+/* One work item of a batched integration: a scan for one map. */
+typedef struct {
+  slim_map* map;
+  const float* pts_dev;
+  int64_t n;
+  double pose[16];
+  const void* sem_dev;
+} slim_batch_item;
+
+/* Integrate n_items scans, possibly of different maps and sizes, with one
+ * launch per phase for all items (work items are scheduled over a shared
+ * persistent grid). Items of the same map are fused as one observation set
+ * (Theorems 1-2 make the result independent of order and grouping). All
+ * maps must live on the current device. Capturable in a CUDA graph when
+ * every map was created before capture. */
+slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items,
+                                 void* stream);
+
+/* Message for the last failure on this thread (never NULL). */
+const char* slim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLIM_GB300_H */

@@ -1,0 +1,96 @@
+// Shared device-side definitions of the scan-integration library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace slim {
+
+constexpr uint64_t kEmptyKey = ~0ull;     // empty hash entry
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu; // hash entry without a block slot
+constexpr int kBlockVoxels = 512;         // 8^3 voxels per block
+constexpr int kBucket = 32;               // hash bucket = one warp
+
+// Device counters held by each map.
+enum Counter : int {
+  kCtrBlocks = 0,   // allocated blocks
+  kCtrRows = 1,     // open set: allocated voxel rows
+  kCtrStatus = 2,   // sticky status (slim_status value of the first fault)
+  kCtrAux = 3,      // diagnostic: where the first fault came from
+  kNumCounters = 8
+};
+
+// Device status codes (same values as slim_status).
+enum DevStatus : uint32_t {
+  kDevOk = 0,
+  kDevCapacity = 3,
+  kDevTimeout = 4,
+  kDevInternal = 7
+};
+
+// Record the first device fault of a map (later faults keep the first).
+__device__ __forceinline__ void raise_status(uint32_t* ctr, uint32_t code, uint32_t where) {
+  if (atomicCAS(&ctr[kCtrStatus], 0u, code) == 0u) ctr[kCtrAux] = where;
+}
+
+// Everything a kernel needs to reach one map's storage.
+struct MapView {
+  uint64_t* hkeys;      // [n_buckets * 32] block keys
+  uint32_t* hvals;      // [n_buckets * 32] block slots
+  uint32_t bucket_mask; // n_buckets - 1 (power of two)
+  int32_t max_probe;    // buckets probed before giving up
+  uint64_t* blk_key;    // [block_cap] key of each allocated slot
+  uint32_t block_cap;
+  uint32_t* ctr;        // kNumCounters counters
+  // closed set: AoS records, rs floats each: {S = W*D, W, c[0..K-1], pad}
+  float* rec;
+  int32_t rs;
+  // open set
+  int32_t* vox_row;     // [block_cap * 512] voxel row or -1
+  float2* tsdf;         // [row_cap] (S = W*D, W)
+  void* mrow;           // [row_cap * L] f32 or bf16 NIG mean
+  void* brow;           // [row_cap * L] f32 or bf16 NIG beta
+  uint32_t row_cap;
+};
+
+// Per-scan geometry: the pose rounded once to float32 and the band.
+struct ScanGeom {
+  float R[9];
+  float t[3];
+  float v;      // voxel size
+  float tau;    // truncation
+  float rmin, rmax;
+  float lim;    // |coordinate| bound: 2^19 voxels
+  int32_t cap;  // DDA step cap: 3 * ceil(2 tau / v) + 3
+};
+
+// Block key: each block coordinate offset by 2^20 into 21 bits, x highest,
+// so the numeric order of keys is the lexicographic order of (bx, by, bz).
+__device__ __forceinline__ uint64_t pack_block(int32_t bx, int32_t by, int32_t bz) {
+  return ((uint64_t)(uint32_t)(bx + (1 << 20)) << 42) |
+         ((uint64_t)(uint32_t)(by + (1 << 20)) << 21) |
+         (uint64_t)(uint32_t)(bz + (1 << 20));
+}
+
+__device__ __forceinline__ void unpack_block(uint64_t k, int32_t& bx, int32_t& by, int32_t& bz) {
+  bx = (int32_t)((k >> 42) & 0x1FFFFF) - (1 << 20);
+  by = (int32_t)((k >> 21) & 0x1FFFFF) - (1 << 20);
+  bz = (int32_t)(k & 0x1FFFFF) - (1 << 20);
+}
+
+__device__ __forceinline__ int local_index(int32_t ix, int32_t iy, int32_t iz) {
+  return ((ix & 7) * 8 + (iy & 7)) * 8 + (iz & 7);
+}
+
+// 64-bit finaliser (splitmix64 style) for bucket selection.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x ^= x >> 31;
+  x *= 0x7FB5D329728EA185ull;
+  x ^= x >> 27;
+  x *= 0x81DADEF4BC2DD44Dull;
+  x ^= x >> 33;
+  return x;
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+}  // namespace slim

@@ -1,0 +1,322 @@
+// Closed-set scan integration (Sec. III-A TSDF + Sec. III-C Dirichlet counts).
+//
+// Two kernels per scan:
+//   k_traverse_alloc  one thread per point: validity, transform, band DDA
+//                     (SDF filter included, so only blocks with a kept
+//                     observation are created), then the warp's distinct
+//                     blocks are inserted into the hash cooperatively and
+//                     new blocks are zero-initialised by the inserting warp.
+//   k_fuse_closed     one 256-point tile per CTA: the DDA is re-run, every
+//                     (voxel, point) pair goes to shared memory as
+//                     (tile block, local voxel, d), the tile's distinct
+//                     blocks are looked up once, the pairs are sorted by
+//                     voxel key (stable CTA radix sort) and reduced per voxel
+//                     segment with warp shuffles; one red.add per voxel (and
+//                     per present class) goes to HBM instead of one atomic
+//                     per pair.
+//
+// Voxel record (AoS, rs floats, 16-byte aligned): {S, W, c_0 .. c_{K-1}, pad}
+// with S = W * D. With w~ = 1 the paper's running average
+// D_t = (W_{t-1} D_{t-1} + d_t) / W_t is the same as S_t = S_{t-1} + d_t,
+// W_t = W_{t-1} + 1 and D = S / W at read-out; keeping S makes every update
+// of a scan an addition, so partial sums from different tiles merge exactly
+// in any order (Theorem 1 for the counts).
+#include "block_sort.cuh"
+#include "common.cuh"
+#include "geometry.cuh"
+#include "hash.cuh"
+#include "internal.h"
+
+namespace slim {
+
+constexpr int kTileCap = 6144;        // (voxel, point) pairs per tile
+constexpr int kTblSize = 2048;        // tile block table (open addressing)
+constexpr int kMaxTileBlocks = 1024;  // distinct blocks per tile
+constexpr int kMaxBandBlocks = 8;     // distinct blocks per point band
+
+// ------------------------------------------------------------------ K1
+__device__ __forceinline__ void zero_block(const MapView& mv, uint32_t slot, bool open) {
+  const unsigned lane = lane_id();
+  if (open) {
+    int4* p = reinterpret_cast<int4*>(mv.vox_row + (size_t)slot * kBlockVoxels);
+    for (int k = lane; k < kBlockVoxels / 4; k += 32) p[k] = make_int4(-1, -1, -1, -1);
+  } else {
+    float4* p = reinterpret_cast<float4*>(mv.rec + (size_t)slot * kBlockVoxels * mv.rs);
+    const int n4 = kBlockVoxels * mv.rs / 4;
+    for (int k = lane; k < n4; k += 32) p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_traverse_alloc(MapView mv, ScanGeom g,
+                                                        const float* __restrict__ pts,
+                                                        int64_t n, int open) {
+  __shared__ uint64_t kbuf[256][kMaxBandBlocks];
+  __shared__ uint32_t s_status;
+  if (threadIdx.x == 0) s_status = *(volatile uint32_t*)&mv.ctr[kCtrStatus];
+  __syncthreads();
+  if (s_status) return;
+  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  int cnt = 0;
+  if (j < n) {
+    Ray ry;
+    if (ray_setup(g, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], ry)) {
+      uint64_t last = kEmptyKey;
+      ray_for_each(g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float) {
+        const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
+        if (kb != last) {
+          if (cnt < kMaxBandBlocks) kbuf[threadIdx.x][cnt] = kb;
+          ++cnt;
+          last = kb;
+        }
+      });
+    }
+  }
+  if (cnt > kMaxBandBlocks) {
+    raise_status(mv.ctr, kDevInternal, 3);
+    cnt = kMaxBandBlocks;
+  }
+  const int maxc = __reduce_max_sync(0xFFFFFFFFu, cnt);
+  for (int r = 0; r < maxc; ++r) {
+    const bool has = r < cnt;
+    const uint64_t key = has ? kbuf[threadIdx.x][r] : 0ull;
+    unsigned pending = __ballot_sync(0xFFFFFFFFu, has);
+    while (pending) {
+      const int src = __ffs(pending) - 1;
+      const uint64_t k = __shfl_sync(0xFFFFFFFFu, key, src);
+      pending &= ~__ballot_sync(0xFFFFFFFFu, has && key == k);
+      warp_insert(mv, k, [&](uint32_t slot) { zero_block(mv, slot, open != 0); });
+    }
+  }
+}
+
+// ------------------------------------------------------------------ K2
+// Insert a block key into the tile's shared table; returns its entry.
+__device__ __forceinline__ uint32_t tbl_insert(uint64_t* tb, uint64_t kb) {
+  uint32_t h = (uint32_t)mix64(kb) & (kTblSize - 1);
+  for (int it = 0; it < kTblSize; ++it) {
+    const uint64_t cur = *(volatile uint64_t*)&tb[h];
+    if (cur == kb) return h;
+    if (cur == kEmptyKey) {
+      const unsigned long long prev = atomicCAS((unsigned long long*)&tb[h],
+                                                (unsigned long long)kEmptyKey,
+                                                (unsigned long long)kb);
+      if (prev == kEmptyKey || prev == kb) return h;
+    }
+    h = (h + 1) & (kTblSize - 1);
+  }
+  return 0xFFFFFFFFu;
+}
+
+size_t closed_smem_bytes(int mode, int K, int tile_points) {
+  size_t b = kTblSize * 8 + kMaxTileBlocks * 4 + kTblSize * 2 + 3 * kTileCap * 4 +
+             256 * kCtaWarps * 4 + 16 * 4 + 256;
+  if (mode == 1) b += (size_t)tile_points * K * 4;
+  return b;
+}
+
+template <int MODE>  // 0: one-hot counts, 1: soft counts
+__global__ void __launch_bounds__(256, 2)
+    k_fuse_closed(MapView mv, ScanGeom g, const float* __restrict__ pts,
+                  const float* __restrict__ sem, int64_t n, int K, int tile_points) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  uint64_t* tb_key = reinterpret_cast<uint64_t*>(sm);
+  uint32_t* tb_slot = reinterpret_cast<uint32_t*>(tb_key + kTblSize);
+  uint16_t* tb_dense = reinterpret_cast<uint16_t*>(tb_slot + kMaxTileBlocks);
+  uint32_t* sA = reinterpret_cast<uint32_t*>(tb_dense + kTblSize);
+  uint32_t* sB = sA + kTileCap;
+  float* pd = reinterpret_cast<float*>(sB + kTileCap);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(pd + kTileCap);
+  uint32_t* wtot = hist + 256 * kCtaWarps;
+  uint32_t* misc = wtot + 8;
+  uint8_t* cls = reinterpret_cast<uint8_t*>(misc + 8);
+  float* probs = reinterpret_cast<float*>(cls + 256);
+
+  const int tid = threadIdx.x;
+  const unsigned lane = lane_id(), warp = tid >> 5;
+  if (tid == 0) {
+    misc[0] = *(volatile uint32_t*)&mv.ctr[kCtrStatus];
+    misc[2] = 0;
+  }
+  for (int e = tid; e < kTblSize; e += kCtaThreads) tb_key[e] = kEmptyKey;
+  __syncthreads();
+  if (misc[0]) return;
+
+  // 1. band DDA: raw pairs at [tid * cap, tid * cap + np)
+  const int64_t j = (int64_t)blockIdx.x * tile_points + tid;
+  const int base = tid * g.cap;
+  int np = 0;
+  uint8_t mycls = 0;
+  if (tid < tile_points && j < n) {
+    Ray ry;
+    if (ray_setup(g, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], ry)) {
+      const float* srow = sem + (size_t)j * K;
+      if (MODE == 0) {
+        int best = 0;
+        float bv = srow[0];
+        for (int k = 1; k < K; ++k) {
+          const float v = srow[k];
+          if (v > bv) {
+            bv = v;
+            best = k;
+          }
+        }
+        mycls = (uint8_t)best;
+      } else {
+        for (int k = 0; k < K; ++k) probs[tid * K + k] = srow[k];
+      }
+      uint64_t last = kEmptyKey;
+      uint32_t last_tb = 0;
+      ray_for_each(g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d) {
+        const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
+        if (kb != last) {
+          last = kb;
+          last_tb = tbl_insert(tb_key, kb);
+          if (last_tb == 0xFFFFFFFFu) misc[2] = 1;
+        }
+        if (last_tb != 0xFFFFFFFFu) {
+          sB[base + np] = (last_tb << 9) | (uint32_t)local_index(i0, i1, i2);
+          pd[base + np] = d;
+          ++np;
+        }
+      });
+    }
+  }
+  cls[tid] = mycls;
+  __syncthreads();
+
+  // 2. dense ids for the tile's blocks (8 table entries per thread)
+  uint64_t* dkey = reinterpret_cast<uint64_t*>(sA);  // dense id -> key (scratch)
+  {
+    uint32_t occ = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) occ += tb_key[tid * 8 + k] != kEmptyKey;
+    uint32_t nb;
+    uint32_t off = cta_exclusive_scan(occ, wtot, &nb);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int e = tid * 8 + k;
+      const uint64_t key = tb_key[e];
+      if (key != kEmptyKey) {
+        tb_dense[e] = (uint16_t)off;
+        if (off < kMaxTileBlocks) dkey[off] = key;
+        ++off;
+      }
+    }
+    if (tid == 0) misc[1] = nb;
+  }
+  uint32_t npairs;
+  const uint32_t poff = cta_exclusive_scan((uint32_t)np, wtot, &npairs);
+  __syncthreads();
+  const uint32_t nb = misc[1];
+  if (nb > kMaxTileBlocks || misc[2]) {
+    if (tid == 0) raise_status(mv.ctr, kDevInternal, 4);
+    return;
+  }
+
+  // 3. one hash lookup per distinct block of the tile
+  for (uint32_t dd = warp; dd < nb; dd += kCtaWarps) {
+    const uint32_t s = warp_find(mv, dkey[dd]);
+    if (lane == 0) tb_slot[dd] = s;
+  }
+  __syncthreads();
+
+  // 4. sort keys: ((dense block << 9 | local) << 13) | raw pair index
+  for (int k = 0; k < np; ++k) {
+    const uint32_t raw = (uint32_t)(base + k);
+    const uint32_t w = sB[raw];
+    const uint32_t key2 = ((uint32_t)tb_dense[w >> 9] << 9) | (w & 511u);
+    sA[poff + k] = (key2 << 13) | raw;
+  }
+  __syncthreads();
+  const int tbits = nb <= 1 ? 0 : 32 - __clz((int)nb - 1);
+  const uint32_t* sorted = cta_radix_sort(sA, sB, (int)npairs, 13, 9 + tbits, hist, wtot);
+
+  // 5. warp segmented reduction over 32-pair windows of the sorted pairs;
+  //    the first lane of each voxel run flushes its sums.
+  for (int wb = (int)warp * 32; wb < (int)npairs; wb += kCtaThreads) {
+    const int i = wb + (int)lane;
+    const bool act = i < (int)npairs;
+    const uint32_t c = act ? sorted[i] : 0u;
+    const uint32_t key2 = act ? (c >> 13) : 0xFFFFFFFFu;
+    const uint32_t raw = c & 0x1FFFu;
+    const int pt = act ? (int)(raw / (uint32_t)g.cap) : 0;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key2);
+    const int first = __ffs(peers) - 1, lastl = 31 - __clz(peers);
+    float dsum = act ? pd[raw] : 0.f;
+    float cnt = act ? 1.f : 0.f;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const float a1 = __shfl_down_sync(0xFFFFFFFFu, dsum, off);
+      const float a2 = __shfl_down_sync(0xFFFFFFFFu, cnt, off);
+      if ((int)lane + off <= lastl) {
+        dsum += a1;
+        cnt += a2;
+      }
+    }
+    const uint32_t slot = act ? tb_slot[key2 >> 9] : kNoSlot;
+    float* r = (slot != kNoSlot) ? mv.rec + ((size_t)slot * kBlockVoxels + (key2 & 511u)) * mv.rs
+                                 : nullptr;
+    if (r && (int)lane == first) {
+      atomicAdd(r, dsum);
+      atomicAdd(r + 1, cnt);
+    }
+    if (MODE == 0) {
+      const uint32_t cl = cls[pt];
+      const uint32_t kc = act ? ((key2 << 7) | cl) : 0xFFFFFFFFu;
+      const unsigned pc = __match_any_sync(0xFFFFFFFFu, kc);
+      if (r && (int)lane == __ffs(pc) - 1) atomicAdd(r + 2 + cl, (float)__popc(pc));
+    } else {
+      for (int k = 0; k < K; ++k) {
+        float pv = act ? probs[pt * K + k] : 0.f;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const float a1 = __shfl_down_sync(0xFFFFFFFFu, pv, off);
+          if ((int)lane + off <= lastl) pv += a1;
+        }
+        if (r && (int)lane == first) atomicAdd(r + 2 + k, pv);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launch
+cudaError_t launch_traverse_alloc(const MapView& mv, const ScanGeom& g, const float* pts,
+                                  int64_t n, bool open, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  k_traverse_alloc<<<grid, 256, 0, st>>>(mv, g, pts, n, open ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t closed_setup_attributes(int mode, int K, int tile_points) {
+  const size_t sm = closed_smem_bytes(mode, K, tile_points);
+  if (mode == 0)
+    return cudaFuncSetAttribute(k_fuse_closed<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sm);
+  return cudaFuncSetAttribute(k_fuse_closed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sm);
+}
+
+int closed_tile_points(int cap, int band_blocks) {
+  int tp = 256;
+  tp = min(tp, (kTileCap / cap) & ~31);
+  tp = min(tp, (kMaxTileBlocks / band_blocks) & ~31);
+  return tp;
+}
+
+int max_band_blocks() { return kMaxBandBlocks; }
+
+cudaError_t launch_fuse_closed(const MapView& mv, const ScanGeom& g, const float* pts,
+                               const float* sem, int64_t n, int mode, int K, int tile_points,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + tile_points - 1) / tile_points);
+  const size_t sm = closed_smem_bytes(mode, K, tile_points);
+  if (mode == 0)
+    k_fuse_closed<0><<<grid, kCtaThreads, sm, st>>>(mv, g, pts, sem, n, K, tile_points);
+  else
+    k_fuse_closed<1><<<grid, kCtaThreads, sm, st>>>(mv, g, pts, sem, n, K, tile_points);
+  return cudaGetLastError();
+}
+
+}  // namespace slim

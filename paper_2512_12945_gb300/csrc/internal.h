@@ -1,0 +1,60 @@
+// Host-side interface between the C ABI (api.cu) and the kernel files.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/slim_gb300.h"
+#include "common.cuh"
+
+namespace slim {
+
+// integrate_closed.cu
+cudaError_t launch_traverse_alloc(const MapView& mv, const ScanGeom& g, const float* pts,
+                                  int64_t n, bool open, cudaStream_t st);
+cudaError_t launch_fuse_closed(const MapView& mv, const ScanGeom& g, const float* pts,
+                               const float* sem, int64_t n, int mode, int K, int tile_points,
+                               cudaStream_t st);
+cudaError_t closed_setup_attributes(int mode, int K, int tile_points);
+int closed_tile_points(int cap, int band_blocks);
+int max_band_blocks();
+
+// device_sort.cu: stable LSD radix sort of (key, value) pairs in global memory
+// over key bits [0, bits). keys/vals are sorted in place using the tmp
+// buffers; temp_bytes tells how much scratch `tmp` needs.
+size_t radix_sort_temp_bytes(int64_t n);
+cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp,
+                           uint32_t* vals_tmp, void* tmp, int64_t n, int bits,
+                           cudaStream_t st);
+cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                           uint32_t* vals_tmp, void* tmp, int64_t n, int bits,
+                           cudaStream_t st);
+// Exclusive scan of n uint32 counts into out (n + 1 entries, out[n] = total).
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp,
+                               cudaStream_t st);
+
+// extract.cu
+struct ExtractArgs {
+  int32_t* ijk;
+  float* D;
+  float* W;
+  float* sem;
+  float* beta;
+  int32_t* index;
+  int32_t flags;
+  int32_t mode;
+  int32_t K;
+  int32_t L;
+  int32_t bf16;
+  float alpha0;
+};
+// Count voxels per sorted block (counts[b]) for b < nb (order = slots[b]).
+cudaError_t launch_extract_count(const MapView& mv, const uint32_t* slots, int64_t nb,
+                                 bool open, uint32_t* counts, cudaStream_t st);
+cudaError_t launch_extract_write(const MapView& mv, const uint32_t* slots,
+                                 const uint64_t* keys, int64_t nb, const uint32_t* offsets,
+                                 const ExtractArgs& a, cudaStream_t st);
+cudaError_t launch_gather_keys(const MapView& mv, int64_t nb, uint64_t* keys, uint32_t* slots,
+                               cudaStream_t st);
+
+}  // namespace slim

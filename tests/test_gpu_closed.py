@@ -1,0 +1,133 @@
+"""Closed-set parity of the CUDA path against the oracle (element by element,
+bit-exact voxel sets, weights and one-hot counts; FP32 D, soft counts and
+posteriors within 1e-5 relative / 1e-6 absolute)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_12945_gb300 import synth
+from helpers import RTOL, ATOL, assert_close, compare_closed, gpu_map, oracle_map, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2512_12945_gb300 import build
+    build.build()
+
+
+def test_room_lidar_onehot():
+    w = synth.room_lidar(n_scans=10)
+    g = to_np(gpu_map(w).extract())
+    o = oracle_map(w).extract()
+    compare_closed(g, o, "onehot")
+    assert np.array_equal(g["sem"].sum(1), g["W"])
+
+
+def test_room_posterior_and_alpha0():
+    w = synth.room_lidar(n_scans=3, n_beams=16, n_az=256)
+    for a0 in (0.0, 1.0):
+        gm = gpu_map(w, alpha0=a0)
+        g = to_np(gm.extract(posterior=True))
+        o = oracle_map(w, alpha0=a0).extract(posterior=True)
+        assert np.array_equal(g["ijk"], o["ijk"])
+        assert_close(g["sem"], o["sem"], RTOL, ATOL, "posterior")
+        assert_close(g["sem"].sum(1), np.ones(len(g["W"])), 1e-5, 1e-6, "posterior sum")
+
+
+def test_street_lidar_reduced():
+    w = synth.street_lidar(n_scans=4, n_beams=64, n_az=512)
+    g = to_np(gpu_map(w).extract())
+    o = oracle_map(w).extract()
+    compare_closed(g, o, "onehot")
+
+
+def test_soft_counts():
+    w = synth.room_lidar(n_scans=4, n_beams=16, n_az=256, K=20, mode="soft")
+    g = to_np(gpu_map(w, mode="soft").extract())
+    o = oracle_map(w, mode="soft").extract()
+    compare_closed(g, o, "soft")
+
+
+def test_ragged_empty_and_invalid():
+    """n = 0, single points, a ragged tail, NaN / out-of-range points."""
+    w = synth.room_lidar(n_scans=2, n_beams=16, n_az=64)
+    s0 = w.scans[0]
+    pts = s0["pts"].copy()
+    pts[5] = np.nan
+    pts[7] = [1e9, 0, 0]
+    pts[9] = [0.01, 0, 0]
+    scans = [dict(pts=pts[:0], pose=s0["pose"], sem=s0["sem"][:0]),
+             dict(pts=pts[:1], pose=s0["pose"], sem=s0["sem"][:1]),
+             dict(pts=pts[:777], pose=s0["pose"], sem=s0["sem"][:777]),
+             w.scans[1]]
+    w.scans = scans
+    g = to_np(gpu_map(w).extract())
+    o = oracle_map(w).extract()
+    compare_closed(g, o, "onehot")
+
+
+def test_empty_map_extract():
+    w = synth.room_lidar(n_scans=1, n_beams=4, n_az=8)
+    w.scans = [dict(pts=np.zeros((0, 3), np.float32), pose=w.scans[0]["pose"],
+                    sem=np.zeros((0, 10), np.float32))]
+    m = gpu_map(w)
+    ext = m.extract()
+    assert ext["W"].shape[0] == 0
+
+
+def test_block_capacity_fault_is_reported():
+    """Too few blocks: the sticky status reports SLIM_ERR_CAPACITY; nothing hangs."""
+    from paper_2512_12945_gb300 import slim
+    w = synth.room_lidar(n_scans=1)
+    m = slim.Map(voxel_size=0.1, trunc=0.3, num_classes=10, min_range=0.1, max_range=100.0,
+                 block_capacity=16, max_points=w.scans[0]["pts"].shape[0])
+    s = w.scans[0]
+    m.integrate(torch.from_numpy(s["pts"]).cuda(), s["pose"], torch.from_numpy(s["sem"]).cuda())
+    with pytest.raises(slim.SlimError) as e:
+        m.sync()
+    assert e.value.status == 3
+    assert m.stats()["status"] == 3
+    m.reset()
+    m.sync()  # reset clears the status
+
+
+def test_host_entry_point_matches_device():
+    w = synth.room_lidar(n_scans=2, n_beams=16, n_az=128)
+    from paper_2512_12945_gb300 import slim
+    a = gpu_map(w)
+    b = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=10, min_range=w.min_range,
+                 max_range=w.max_range, max_points=w.scans[0]["pts"].shape[0])
+    for s in w.scans:
+        b.integrate_host(torch.from_numpy(s["pts"]).pin_memory(), s["pose"],
+                         torch.from_numpy(s["sem"]).pin_memory())
+    b.sync()
+    ga, gb = to_np(a.extract()), to_np(b.extract())
+    assert np.array_equal(ga["ijk"], gb["ijk"]) and np.array_equal(ga["W"], gb["W"])
+    assert_close(ga["D"], gb["D"], RTOL, ATOL, "D")
+
+
+def test_full_size_street_scans_parity():
+    """Full launch configuration: 64 x 2048 scans (131,072 points per call)."""
+    w = synth.street_lidar(n_scans=2)
+    g = to_np(gpu_map(w).extract())
+    o = oracle_map(w).extract()
+    compare_closed(g, o, "onehot")
+
+
+def test_full_size_100_scans_invariants():
+    """The benchmark workload (100 full scans): every voxel has sum c = W, D in
+    [-tau, tau], and the total weight equals the oracle's pair count."""
+    w = synth.street_lidar(n_scans=100)
+    g = to_np(gpu_map(w, block_capacity=400000, hash_capacity=1 << 21).extract())
+    assert np.array_equal(g["sem"].sum(1), g["W"])
+    assert (np.abs(g["D"]) <= np.float32(0.3) + 1e-6).all()
+    p = oracle.make_params(w.voxel_size, w.trunc, num_classes=20, min_range=w.min_range,
+                           max_range=w.max_range, body_from_sensor=w.body_from_sensor)
+    total = 0
+    for s in w.scans[::10]:
+        total += len(oracle.scan_pairs(p, s["pts"], s["pose"])[2])
+    sub = gpu_map(w, scans=w.scans[::10], block_capacity=400000, hash_capacity=1 << 21)
+    assert float(to_np(sub.extract())["W"].sum()) == total
