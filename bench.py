@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Throughput of scan integration (points integrated per second) on GB300.
+
+Workload: the urban LiDAR sequence — 100 scans of 64 beams x 2048 azimuths
+(131,072 points per scan, ~120k valid, ranges 1-80 m) ray-cast in a seeded
+synthetic street, 0.1 m voxels, 0.3 m truncation, 20 classes (closed-set
+one-hot Dirichlet counts). One step = empty the map and integrate all 100
+scans through the C ABI (slim_integrate per scan) with inputs resident in
+HBM (1.2 GB per step, larger than L2, so every step streams from HBM).
+
+Prints one JSON line. Extra keys: roofline (dominant kernel, algorithmic
+bytes from the oracle's stored per-scan counts / CUDA-event kernel time in
+the timed region), e2e (slim_integrate_host from pinned host buffers, H2D
+copies and a D2H read of the map counters inside the timed region),
+cpu_baseline (the oracle on a bounded sample, host cores), clocks.
+
+--impl reference times the oracle (plain sequential CPU restatement) on
+this host, one full scan per step.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "points integrated/s (TSDF+Bayes semantic), % HBM roofline, plain vs chosen"
+UNIT = "points/s"
+COUNTS = os.path.join(ROOT, "tests", "golden", "street_lidar_counts.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+K_CLASSES = 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scans", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="0: same as --steps (max 10)")
+    return ap.parse_args()
+
+
+def workload_config(n_scans):
+    return {"workload": f"street-lidar {n_scans} scans x 64x2048 (131072 pts/scan), "
+                        "voxel 0.1 m, trunc 0.3 m, 20 classes one-hot",
+            "scans": n_scans, "points_per_scan": 131072, "voxel_size": 0.1, "trunc": 0.3,
+            "classes": K_CLASSES, "semantics": "closed-set one-hot Dirichlet",
+            "l2": "inputs larger than L2 (1.21 GB per step)", "parallelism": "replicas"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+        self.marks = {}
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu=timestamp,{self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "50"]
+        if self.uuid:
+            cmd.insert(1, f"--id={self.uuid}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, name):
+        self.marks[name] = time.time()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        t0, t1 = self.marks.get("t0", 0), self.marks.get("t1", 1e30)
+        rows = [l for (t, l) in self.lines if t0 <= t <= t1] or [l for _, l in self.lines]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in rows:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(counts, n_scans):
+    """B = N_all*12 + N_valid*4K + (2*U_old + U_new)*R + U_b*16 per scan,
+    R = 8 + 4K bytes (D, W, K counts)."""
+    R = 8 + 4 * K_CLASSES
+    out = []
+    for row in counts["scans"][:n_scans]:
+        old = row["voxels"] - row["new_voxels"]
+        out.append(row["points"] * 12 + row["valid"] * 4 * K_CLASSES +
+                   (2 * old + row["new_voxels"]) * R + row["blocks"] * 16)
+    return out
+
+
+def kernel_source_sha():
+    p = os.path.join(ROOT, "paper_2512_12945_gb300", "csrc", "integrate_closed.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def stored_traffic():
+    try:
+        with open(TRAFFIC) as f:
+            t = json.load(f)
+        if t.get("source_sha") == kernel_source_sha():
+            return t.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def cpu_oracle_rate(w, n_scans):
+    """The oracle as it stands, on the first n_scans of the workload."""
+    import oracle
+    m = oracle.OracleMap(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=w.num_classes,
+                         min_range=w.min_range, max_range=w.max_range,
+                         body_from_sensor=w.body_from_sensor)
+    t = time.perf_counter()
+    valid = 0
+    for s in w.scans[:n_scans]:
+        valid += m.integrate(s["pts"], s["pose"], s["sem"])
+    dt = time.perf_counter() - t
+    return valid / dt, dt, valid
+
+
+# --------------------------------------------------------------- reference
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2512_12945_gb300 import synth
+    n = args.steps + args.warmup
+    w = synth.street_lidar(n_scans=min(n, args.scans))
+    import oracle
+    times, valids = [], []
+    for k in range(n):
+        s = w.scans[k % len(w.scans)]
+        m = oracle.OracleMap(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=w.num_classes,
+                             min_range=w.min_range, max_range=w.max_range,
+                             body_from_sensor=w.body_from_sensor)
+        t = time.perf_counter()
+        v = m.integrate(s["pts"], s["pose"], s["sem"])
+        dt = time.perf_counter() - t
+        if k >= args.warmup:
+            times.append(dt)
+            valids.append(v)
+    tot = sum(times)
+    value = sum(valids) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.scans),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one full 64x2048 scan into an empty map per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2512_12945_gb300 import build, slim, synth
+    if rank == 0 or ws == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+    L = slim.lib()
+
+    w = synth.street_lidar(n_scans=args.scans)
+    m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=w.num_classes,
+                 min_range=w.min_range, max_range=w.max_range, body_from_sensor=w.body_from_sensor,
+                 block_capacity=400000, hash_capacity=1 << 21, max_points=131072)
+    h = m.handle
+    pts = [torch.from_numpy(s["pts"]).cuda() for s in w.scans]
+    sem = [torch.from_numpy(s["sem"]).cuda() for s in w.scans]
+    tile = m.autotune(pts[len(pts) // 2], w.scans[len(pts) // 2]["pose"], sem[len(pts) // 2])
+    poses = [np.ascontiguousarray(np.asarray(s["pose"], np.float64).reshape(16)) for s in w.scans]
+    args_c = [(ctypes.c_void_p(p.data_ptr()), p.shape[0], po.ctypes.data_as(ctypes.c_void_p),
+               ctypes.c_void_p(se.data_ptr())) for p, se, po in zip(pts, sem, poses)]
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def step():
+        L.slim_map_reset(h, sp)
+        for a in args_c:
+            rc = L.slim_integrate(h, a[0], a[1], a[2], a[3], sp)
+            if rc:
+                raise slim.SlimError(rc, L.slim_last_error().decode())
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if uuid and not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    m.sync()
+    slim.slim_profile_enable(h, True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.mark("t0")
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks.mark("t1")
+    ms = ev0.elapsed_time(ev1)
+    prof = slim.slim_profile_read(h)
+    slim.slim_profile_enable(h, False)
+    m.sync()
+    clocks.stop()
+    stats = m.stats()
+
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+
+    counts = None
+    try:
+        with open(COUNTS) as f:
+            counts = json.load(f)
+    except OSError:
+        pass
+    if counts is not None:
+        valid_per_step = sum(r["valid"] for r in counts["scans"][:args.scans])
+    else:
+        valid_per_step = int(sum(int((np.linalg.norm(s["pts"], axis=1) >= w.min_range).sum())
+                                 for s in w.scans))
+    value = ws * valid_per_step * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (fuse_closed): algorithmic bytes / event time
+    roof = None
+    peak, peak_kind = measured_peak()
+    if counts is not None and "fuse_closed" in prof:
+        nl, kms = prof["fuse_closed"]
+        B = algorithmic_bytes(counts, args.scans)
+        bytes_per_launch = sum(B) / len(B)
+        avg_ms = kms / nl
+        achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": stored_traffic(),
+                "kernel": "k_fuse_closed", "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": int(bytes_per_launch),
+                "avg_launch_ms": round(avg_ms, 5),
+                "path_frac": round(sum(B) * args.steps / (ms / 1e3) / 1e9 / peak, 4)}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    n_e2e = args.e2e_steps or min(args.steps, 10)
+    pts_h = [torch.from_numpy(s["pts"]).pin_memory() for s in w.scans]
+    sem_h = [torch.from_numpy(s["sem"]).pin_memory() for s in w.scans]
+    st_c = slim.slim_stats()
+    h2d = sum(p.numel() * 4 + q.numel() * 4 for p, q in zip(pts_h, sem_h))
+
+    def step_host():
+        L.slim_map_reset(h, sp)
+        for p, q, po in zip(pts_h, sem_h, poses):
+            rc = L.slim_integrate_host(h, ctypes.c_void_p(p.data_ptr()), p.shape[0],
+                                       po.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.c_void_p(q.data_ptr()), sp)
+            if rc:
+                raise slim.SlimError(rc, L.slim_last_error().decode())
+        rc = L.slim_map_stats(h, ctypes.byref(st_c), sp)  # D2H of the map counters
+        if rc:
+            raise slim.SlimError(rc, L.slim_last_error().decode())
+
+    step_host()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_e2e):
+        step_host()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    e_ms = max(e0.elapsed_time(e1), wall * 1e3)
+    et = torch.tensor([e_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e_ms = float(et.item())
+    e2e = {"value": ws * valid_per_step * n_e2e / (e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * 4, "steps": n_e2e,
+           "call": "slim_integrate_host x scans + slim_map_stats"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_cpu = 4
+        rate, dt, nv = cpu_oracle_rate(w, n_cpu)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {n_cpu} scans of the workload ({nv} valid points), "
+                         f"{dt:.1f} s single-threaded"}
+
+    # the other aggregation strategy on the same workload ("plain vs chosen")
+    variants = {}
+    for agg in ("sort",):
+        mv = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=w.num_classes,
+                      min_range=w.min_range, max_range=w.max_range,
+                      body_from_sensor=w.body_from_sensor, block_capacity=400000,
+                      hash_capacity=1 << 21, max_points=131072, aggregation=agg)
+        hv = mv.handle
+
+        def step_v():
+            L.slim_map_reset(hv, sp)
+            for a in args_c:
+                L.slim_integrate(hv, a[0], a[1], a[2], a[3], sp)
+
+        for _ in range(2):
+            step_v()
+        torch.cuda.synchronize()
+        nv = max(2, min(args.steps, 5))
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(nv):
+            step_v()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        mv.sync()
+        vms = a0.elapsed_time(a1) / nv
+        variants[agg] = {"value": valid_per_step / (vms / 1e3), "ms_per_step": vms, "steps": nv}
+        mv.close()
+
+    launches = sum(v[0] for v in prof.values())
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args.scans), "roofline": roof, "cpu_baseline": cpu,
+            "e2e": e2e, "clocks": clocks.summary(), "gpu_launches": launches,
+            "kernels_ms": {k: round(v[1], 3) for k, v in prof.items()},
+            "aggregation": "hash (shared-memory (voxel, class) table)", "tile_points": tile,
+            "variants": variants,
+            "map": {"blocks": stats["blocks"],
+                    "oracle_voxels": counts["meta"]["total_voxels"] if counts else None}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -18,10 +18,11 @@
  *   - Arguments are checked on the host before anything is queued; a bad
  *     argument returns SLIM_ERR_ARG and queues nothing.
  *   - Faults found on the device (capacity exhausted, a bounded probe or wait
- *     that ran out) set a sticky status word in the map. Kernels of a scan
- *     that sees a non-zero status leave the voxel fields untouched. The status
- *     is returned by slim_map_sync and by the next call that synchronises;
- *     slim_map_reset clears it.
+ *     that ran out) set a sticky status word in the map. The scan during
+ *     which the fault happens may be partly applied; every later scan sees
+ *     the status and leaves the voxel fields untouched. The status is
+ *     returned by slim_map_sync and by the calls that synchronise (stats,
+ *     extract, query); slim_map_reset clears it.
  *   - No exception or longjmp crosses this boundary. A map handle must not be
  *     used from two host threads at once.
  *   - slim_last_error() gives a human-readable message for the last failure
@@ -63,6 +64,16 @@ typedef enum {
 
 typedef enum { SLIM_STORE_F32 = 0, SLIM_STORE_BF16 = 1 } slim_storage;
 
+/* How a closed-set tile groups its (voxel, point) pairs before the one
+ * global update per voxel (both give the same result; Theorem 1 makes the
+ * grouping free):
+ *   SLIM_AGG_SORT  stable CTA radix sort of the pairs by voxel key, then a
+ *                  warp segmented reduction over each voxel's run;
+ *   SLIM_AGG_HASH  one-hot only: each pair is added at once into a
+ *                  shared-memory table keyed by (voxel, class);
+ *   SLIM_AGG_AUTO  hash for one-hot, sort for soft counts. */
+typedef enum { SLIM_AGG_AUTO = 0, SLIM_AGG_SORT = 1, SLIM_AGG_HASH = 2 } slim_aggregation;
+
 typedef struct {
   float voxel_size;      /* metres, > 0 */
   float trunc;           /* truncation tau in metres, 0 < tau <= 4 voxel_size */
@@ -74,10 +85,13 @@ typedef struct {
   int32_t embed_storage; /* slim_storage of m and beta (SLIM_OPEN) */
   double alpha0;         /* Dirichlet prior per class, >= 0 (read-out only) */
   double body_from_sensor[16]; /* row-major 4x4 extrinsic, FP64 */
-  int64_t block_capacity;  /* maximum allocated 8^3 blocks */
+  int64_t block_capacity;  /* maximum allocated 8^3 blocks, < 2^23 */
   int64_t hash_capacity;   /* hash entries (rounded up to 32 x power of 2) */
   int64_t voxel_capacity;  /* SLIM_OPEN: maximum allocated voxels */
   int64_t max_points;      /* largest scan passed to slim_integrate */
+  int32_t aggregation;     /* slim_aggregation: how a tile groups its pairs */
+  int32_t tile_points;     /* hash aggregation: points per CTA tile, 64, 128 or
+                              256 (0 = 256); see slim_autotune */
 } slim_map_params;
 
 typedef struct slim_map slim_map;
@@ -117,7 +131,8 @@ slim_status slim_map_reset(slim_map* m, void* stream);
  *   with along-ray SDF d = (x - c) . u >= -tau receives one observation
  *   min(d, tau) and the point's semantics:
  *     closed modes: sem_dev = n x K float32 class probabilities (row-major);
- *     SLIM_OPEN:    sem_dev = n x l float32 embeddings (row-major).
+ *     SLIM_OPEN:    sem_dev = n x l float32 embeddings (row-major, 16-byte
+ *                   aligned).
  * Fusion: W += 1, D running average (w~ = 1), then the mode's update.
  * n may be 0. n <= max_points. Asynchronous on `stream`. */
 slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
@@ -205,6 +220,38 @@ typedef struct {
  * every map was created before capture. */
 slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items,
                                  void* stream);
+
+/* Tile-size autotuner (no counterpart in the paper). For a closed-set
+ * one-hot map with hash aggregation, integrates the given scan (same
+ * arguments as slim_integrate) repeatedly with every tile size (64, 128 and
+ * 256 points per CTA), times each with CUDA events on `stream`, keeps the
+ * fastest for this map and writes it to *best_tile (may be NULL). The map is
+ * reset (emptied) before each trial and at the end. Synchronous. Other maps
+ * return SLIM_ERR_UNSUPPORTED. */
+slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
+                          const double pose_host[16], const void* sem_dev, void* stream,
+                          int32_t* best_tile);
+
+/* Kernel kinds reported by slim_profile_read. */
+typedef enum {
+  SLIM_KERNEL_TRAVERSE = 0,     /* band DDA + block allocation */
+  SLIM_KERNEL_FUSE_CLOSED = 1,  /* closed-set tile sort + segmented reduce */
+  SLIM_KERNEL_OPEN_PAIRS = 2,   /* open-set pair generation + voxel sort */
+  SLIM_KERNEL_OPEN_APPLY = 3,   /* open-set segmented NIG apply */
+  SLIM_KERNEL_QUERY = 4,        /* tensor-core query GEMM + epilogue */
+  SLIM_KERNEL_BACKWARD = 5,     /* adjoint gather */
+  SLIM_KERNEL_BATCH = 6,        /* batched persistent integration */
+  SLIM_KERNEL_KINDS = 8
+} slim_kernel;
+
+/* Measurement aid (no counterpart in the paper). With on != 0 every kernel
+ * the map launches is bracketed by two CUDA events recorded on its launch
+ * stream. slim_profile_read waits for those events and writes, per kernel
+ * kind, the number of launches and their summed device time in ms since the
+ * last read; it then clears the record. launches and ms each hold
+ * SLIM_KERNEL_KINDS entries (caller-owned host arrays). */
+slim_status slim_profile_enable(slim_map* m, int32_t on);
+slim_status slim_profile_read(slim_map* m, int64_t* launches, double* ms);
 
 /* Message for the last failure on this thread (never NULL). */
 const char* slim_last_error(void);

@@ -1,0 +1,135 @@
+// Reverse mode of scan integration for a map integrated from empty (zero
+// priors: the final state is the batch posterior of all observations,
+// Theorems 1-2). For one scan, per point j and each of its (voxel v, point j)
+// observations, recomputed by the same band DDA as the forward pass:
+//   D_v = (sum d) / W_v         ->  dL/dd_vj = dL/dD_v / W_v  (0 if d clamped)
+//   d = (x - c_v) . u, u = (x - o) / r
+//                               ->  dd/dx = u + (I - u u^T)(x - c_v) / r
+//   x = R p + t                 ->  dL/dp = R^T dL/dx
+//   closed soft: c_v = sum p_j  ->  dL/dp_j += dL/dc_v
+//   open: m_v = sum z / W_v, beta_v = 1/2 sum (z - m_v)^2
+//                               ->  dL/dz_j += dL/dm_v / W_v
+//                                              + dL/dbeta_v * (z_j - m_v)
+// One warp per point: every lane walks the same DDA, lanes split the class
+// or embedding dimension; the result is a gather (the adjoint of the
+// forward scatter), so no atomics are needed.
+#include <cuda_bf16.h>
+
+#include "geometry.cuh"
+#include "hash.cuh"
+#include "map.h"
+
+namespace slim {
+
+template <int OPEN, int BF16>
+__global__ void __launch_bounds__(256) k_backward(MapView mv, ScanGeom g,
+                                                  const float* __restrict__ pts,
+                                                  const float* __restrict__ sem, int64_t n,
+                                                  int width, const float* __restrict__ gD,
+                                                  const float* __restrict__ gS,
+                                                  const float* __restrict__ gB, float* gsem,
+                                                  float* gxyz, int sem_grad) {
+  const unsigned lane = lane_id();
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= n) return;
+  float acc[32];  // this lane's share of dL/dsem_j: elements lane + 32 k
+  const int per = (width + 31) / 32;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+  float gx0 = 0.f, gx1 = 0.f, gx2 = 0.f;
+  Ray ry;
+  const bool valid = ray_setup(g, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], ry);
+  if (valid) {
+    const float* zrow = sem + (size_t)j * width;
+    uint64_t last = kEmptyKey;
+    uint32_t slot = kNoSlot;
+    ray_for_each(g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d) {
+      const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
+      if (kb != last) {
+        last = kb;
+        slot = hash_find(mv, kb);
+      }
+      if (slot == kNoSlot) return;
+      const size_t vox = (size_t)slot * kBlockVoxels + local_index(i0, i1, i2);
+      float Wv;
+      size_t gi;
+      if (OPEN) {
+        const int32_t row = mv.vox_row[vox];
+        if (row < 0) return;
+        Wv = mv.tsdf[row].y;
+        gi = (size_t)row;
+      } else {
+        Wv = mv.rec[vox * mv.rs + 1];
+        gi = vox;
+      }
+      const float invW = 1.0f / Wv;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if (k >= per || !sem_grad) break;
+        const int e = (int)lane + 32 * k;
+        if (e >= width) break;
+        const size_t o = gi * (size_t)width + e;
+        if (OPEN) {
+          float gm = gS[o] * invW;
+          if (gB) {
+            const float mval = BF16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(mv.mrow)[o])
+                                    : static_cast<const float*>(mv.mrow)[o];
+            gm += gB[o] * (zrow[e] - mval);
+          }
+          acc[k] += gm;
+        } else {
+          acc[k] += gS[o];
+        }
+      }
+      if (!(d < g.tau)) return;  // clamped at tau: no dependence on x
+      const float gd = gD[gi] * invW;
+      const float c0 = ((float)i0 + 0.5f) * g.v, c1 = ((float)i1 + 0.5f) * g.v,
+                  c2 = ((float)i2 + 0.5f) * g.v;
+      const float e0 = ry.x0 - c0, e1 = ry.x1 - c1, e2 = ry.x2 - c2;
+      const float eu = e0 * ry.u0 + e1 * ry.u1 + e2 * ry.u2;
+      const float ir = 1.0f / ry.r;
+      gx0 += gd * (ry.u0 + (e0 - ry.u0 * eu) * ir);
+      gx1 += gd * (ry.u1 + (e1 - ry.u1 * eu) * ir);
+      gx2 += gd * (ry.u2 + (e2 - ry.u2 * eu) * ir);
+    });
+  }
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k >= per) break;
+    const int e = (int)lane + 32 * k;
+    if (e < width) gsem[(size_t)j * width + e] = acc[k];
+  }
+  if (lane == 0) {
+    // dL/dp = R^T dL/dx
+    gxyz[3 * j + 0] = g.R[0] * gx0 + g.R[3] * gx1 + g.R[6] * gx2;
+    gxyz[3 * j + 1] = g.R[1] * gx0 + g.R[4] * gx1 + g.R[7] * gx2;
+    gxyz[3 * j + 2] = g.R[2] * gx0 + g.R[5] * gx1 + g.R[8] * gx2;
+  }
+}
+
+slim_status run_backward(slim_map* m, const ScanGeom& g, const float* pts, const float* sem,
+                         int64_t n, const float* gD, const float* gS, const float* gB,
+                         float* gsem, float* gxyz, cudaStream_t st) {
+  if (n <= 0) return SLIM_OK;
+  const int width = m->mode == SLIM_OPEN ? m->L : m->K;
+  const unsigned grid = (unsigned)((n * 32 + 255) / 256);
+  const int tok = prof_begin(m, SLIM_KERNEL_BACKWARD, st);
+  const int sg = m->mode == SLIM_CLOSED_ONEHOT ? 0 : 1;  // argmax has no gradient
+  if (m->mode == SLIM_OPEN) {
+    if (m->bf16)
+      k_backward<1, 1><<<grid, 256, 0, st>>>(m->mv, g, pts, sem, n, width, gD, gS, gB, gsem, gxyz,
+                                             sg);
+    else
+      k_backward<1, 0><<<grid, 256, 0, st>>>(m->mv, g, pts, sem, n, width, gD, gS, gB, gsem, gxyz,
+                                             sg);
+  } else {
+    k_backward<0, 0><<<grid, 256, 0, st>>>(m->mv, g, pts, sem, n, width, gD, gS, gB, gsem, gxyz,
+                                           sg);
+  }
+  prof_end(m, tok, st);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  return SLIM_OK;
+}
+
+}  // namespace slim

@@ -40,6 +40,29 @@ uint64_t next_pow2(uint64_t x) {
 }
 }  // namespace
 
+namespace slim {
+int prof_begin(slim_map* m, int kind, cudaStream_t st) {
+  if (!m->prof_on) return -1;
+  const size_t k = m->prof_used;
+  if (2 * k + 1 >= m->prof_ev.size()) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      m->prof_ev.push_back(e);
+    }
+    m->prof_kind.push_back(kind);
+  }
+  m->prof_kind[k] = kind;
+  m->prof_used = k + 1;
+  cudaEventRecord(m->prof_ev[2 * k], st);
+  return (int)k;
+}
+
+void prof_end(slim_map* m, int token, cudaStream_t st) {
+  if (token >= 0) cudaEventRecord(m->prof_ev[2 * token + 1], st);
+}
+}  // namespace slim
+
 namespace {
 
 int sem_width(const slim_map* m) { return m->mode == SLIM_OPEN ? m->L : m->K; }
@@ -110,12 +133,19 @@ slim_status check_params(const slim_map_params* p) {
   if (!(p->alpha0 >= 0.0) || !std::isfinite(p->alpha0))
     return fail(SLIM_ERR_ARG, "alpha0 must be finite and >= 0");
   if (!finite_pose(p->body_from_sensor)) return fail(SLIM_ERR_ARG, "extrinsic not finite");
-  if (p->block_capacity < 1 || p->block_capacity > (int64_t)(1u << 23))
-    return fail(SLIM_ERR_ARG, "block_capacity must be in [1, 2^23]");
+  if (p->block_capacity < 1 || p->block_capacity >= (int64_t)(1u << 23))
+    return fail(SLIM_ERR_ARG, "block_capacity must be in [1, 2^23)");
   if (p->hash_capacity < 32 || p->hash_capacity > ((int64_t)1 << 32))
     return fail(SLIM_ERR_ARG, "hash_capacity must be in [32, 2^32]");
   if (p->max_points < 0 || p->max_points > ((int64_t)1 << 31))
     return fail(SLIM_ERR_ARG, "max_points must be in [0, 2^31]");
+  if (p->tile_points != 0 && p->tile_points != 64 && p->tile_points != 128 &&
+      p->tile_points != 256)
+    return fail(SLIM_ERR_ARG, "tile_points must be 0 (default), 64, 128 or 256");
+  if (p->aggregation < 0 || p->aggregation > 2)
+    return fail(SLIM_ERR_ARG, "aggregation must be 0 (auto), 1 (sort) or 2 (hash)");
+  if (p->aggregation == SLIM_AGG_HASH && p->mode != SLIM_CLOSED_ONEHOT)
+    return fail(SLIM_ERR_ARG, "hash aggregation serves the closed one-hot mode only");
   return SLIM_OK;
 }
 
@@ -168,8 +198,9 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
     return fail(SLIM_ERR_ARG, "trunc / voxel_size too large");
   }
   m->tile_points = closed_tile_points(m->cap, m->band_blocks);
-  m->n_buckets = (uint32_t)next_pow2((uint64_t)((p->hash_capacity + 31) / 32));
-  const uint64_t nh = (uint64_t)m->n_buckets * kBucket;
+  m->hash_tile = p->tile_points > 0 ? p->tile_points : 256;
+  m->n_entries = next_pow2((uint64_t)p->hash_capacity);
+  const uint64_t nh = m->n_entries;
   const uint64_t bc = (uint64_t)p->block_capacity;
 
   auto bail = [&](slim_status st) {
@@ -182,8 +213,8 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   if ((s = m->alloc(&mv.hvals, nh)) != SLIM_OK) return bail(s);
   if ((s = m->alloc(&mv.blk_key, bc)) != SLIM_OK) return bail(s);
   if ((s = m->alloc(&mv.ctr, (size_t)kNumCounters)) != SLIM_OK) return bail(s);
-  mv.bucket_mask = m->n_buckets - 1;
-  mv.max_probe = (int32_t)std::min<uint64_t>(m->n_buckets, 64);
+  mv.entry_mask = (uint32_t)(m->n_entries - 1);
+  mv.max_probe = (int32_t)std::min<uint64_t>(m->n_entries, 512);
   mv.block_cap = (uint32_t)bc;
   mv.rs = m->rs;
   if (m->mode != SLIM_OPEN) {
@@ -200,6 +231,14 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
     mv.mrow = mr;
     mv.brow = br;
     mv.row_cap = (uint32_t)rc;
+    if ((s = m->alloc(&mv.mnorm2, rc)) != SLIM_OK) return bail(s);
+    if ((s = m->alloc(&m->qscratch.qinv, (size_t)256)) != SLIM_OK) return bail(s);
+    if (!m->bf16) {
+      unsigned char* abf = nullptr;
+      if ((s = m->alloc(&abf, rc * m->L * 2)) != SLIM_OK) return bail(s);
+      m->qscratch.abf = abf;
+      if ((s = m->alloc(&m->qscratch.rnorm2, rc)) != SLIM_OK) return bail(s);
+    }
     if ((s = open_alloc_scratch(m, m->open, p->max_points)) != SLIM_OK) return bail(s);
   }
   const int64_t mp = std::max<int64_t>(p->max_points, 1);
@@ -222,7 +261,10 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   std::memset(m->pinned, 0, kNumCounters * sizeof(uint32_t));
   cudaError_t e = cudaSuccess;
   if (m->mode != SLIM_OPEN) e = closed_setup_attributes(m->mode, m->K, m->tile_points);
-  else e = open_setup_attributes(m);
+  else {
+    e = open_setup_attributes(m);
+    if (e == cudaSuccess) e = query_setup_attributes();
+  }
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute"));
   if ((s = slim_map_reset(m, nullptr)) != SLIM_OK) return bail(s);
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "sync"));
@@ -241,7 +283,7 @@ slim_status slim_map_destroy(slim_map* m) {
 slim_status slim_map_reset(slim_map* m, void* stream) {
   if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t nh = (size_t)m->n_buckets * kBucket;
+  const size_t nh = (size_t)m->n_entries;
   SLIM_CUDA(cudaMemsetAsync(m->mv.hkeys, 0xFF, nh * sizeof(uint64_t), st));
   SLIM_CUDA(cudaMemsetAsync(m->mv.hvals, 0xFF, nh * sizeof(uint32_t), st));
   SLIM_CUDA(cudaMemsetAsync(m->mv.ctr, 0, kNumCounters * sizeof(uint32_t), st));
@@ -257,6 +299,8 @@ slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
   if (n > 0 && (!pts_dev || !sem_dev)) return fail(SLIM_ERR_ARG, "pts/sem NULL with n > 0");
   if ((reinterpret_cast<uintptr_t>(pts_dev) & 3) || (reinterpret_cast<uintptr_t>(sem_dev) & 3))
     return fail(SLIM_ERR_ARG, "pts/sem must be 4-byte aligned");
+  if (m->mode == SLIM_OPEN && (reinterpret_cast<uintptr_t>(sem_dev) & 15))
+    return fail(SLIM_ERR_ARG, "open-set embeddings must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
   ScanGeom g;
   compose_pose(pose_host, m->p.body_from_sensor, g, m->p.voxel_size, m->p.trunc,
@@ -264,11 +308,19 @@ slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
   m->scans++;
   if (n == 0) return SLIM_OK;
   const float* sem = static_cast<const float*>(sem_dev);
-  SLIM_CUDA(launch_traverse_alloc(m->mv, g, pts_dev, n, m->mode == SLIM_OPEN, st));
   if (m->mode != SLIM_OPEN) {
-    SLIM_CUDA(launch_fuse_closed(m->mv, g, pts_dev, sem, n, m->mode, m->K, m->tile_points, st));
+    const int tok = prof_begin(m, SLIM_KERNEL_FUSE_CLOSED, st);
+    if (m->mode == SLIM_CLOSED_ONEHOT && m->p.aggregation != SLIM_AGG_SORT)
+      SLIM_CUDA(launch_fuse_hash(m->mv, g, pts_dev, sem, n, m->K, m->hash_tile, m->band_blocks,
+                                 st));
+    else
+      SLIM_CUDA(launch_fuse_closed(m->mv, g, pts_dev, sem, n, m->mode, m->K, m->tile_points, st));
+    prof_end(m, tok, st);
     return SLIM_OK;
   }
+  const int tok = prof_begin(m, SLIM_KERNEL_TRAVERSE, st);
+  SLIM_CUDA(launch_traverse_alloc(m->mv, g, pts_dev, n, true, st));
+  prof_end(m, tok, st);
   return open_integrate(m, m->mv, m->open, g, pts_dev, sem, n, m->L, m->bf16, st);
 }
 
@@ -286,6 +338,79 @@ slim_status slim_integrate_host(slim_map* m, const float* pts_host, int64_t n,
                               cudaMemcpyHostToDevice, st));
   }
   return slim_integrate(m, m->stage_pts, n, pose_host, m->stage_sem, stream);
+}
+
+slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
+                          const double pose_host[16], const void* sem_dev, void* stream,
+                          int32_t* best_tile) {
+  if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
+  if (m->mode != SLIM_CLOSED_ONEHOT || m->p.aggregation == SLIM_AGG_SORT)
+    return fail(SLIM_ERR_UNSUPPORTED, "autotune serves closed one-hot maps with hash aggregation");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int saved = m->hash_tile;
+  const bool prof = m->prof_on;
+  m->prof_on = false;
+  cudaEvent_t e0, e1;
+  SLIM_CUDA(cudaEventCreate(&e0));
+  SLIM_CUDA(cudaEventCreate(&e1));
+  const int cand[3] = {64, 128, 256};
+  float best_ms = 1e30f;
+  int best = saved;
+  slim_status s = SLIM_OK;
+  for (int c = 0; c < 3 && s == SLIM_OK; ++c) {
+    m->hash_tile = cand[c];
+    if ((s = slim_map_reset(m, stream)) != SLIM_OK) break;
+    for (int w = 0; w < 3 && s == SLIM_OK; ++w) s = slim_integrate(m, pts_dev, n, pose_host, sem_dev, stream);
+    if (s != SLIM_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 5 && s == SLIM_OK; ++r) s = slim_integrate(m, pts_dev, n, pose_host, sem_dev, stream);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      s = cuda_fail(cudaGetLastError(), "autotune");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->prof_on = prof;
+  m->hash_tile = s == SLIM_OK ? best : saved;
+  const slim_status r = slim_map_reset(m, stream);
+  if (s != SLIM_OK) return s;
+  if (r != SLIM_OK) return r;
+  SLIM_CUDA(cudaStreamSynchronize(st));
+  if (best_tile) *best_tile = m->hash_tile;
+  return SLIM_OK;
+}
+
+slim_status slim_profile_enable(slim_map* m, int32_t on) {
+  if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
+  m->prof_on = on != 0;
+  m->prof_used = 0;
+  return SLIM_OK;
+}
+
+slim_status slim_profile_read(slim_map* m, int64_t* launches, double* ms) {
+  if (!m || !launches || !ms) return fail(SLIM_ERR_ARG, "map, launches or ms is NULL");
+  for (int k = 0; k < SLIM_KERNEL_KINDS; ++k) {
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+  for (size_t k = 0; k < m->prof_used; ++k) {
+    SLIM_CUDA(cudaEventSynchronize(m->prof_ev[2 * k + 1]));
+    float t = 0.f;
+    SLIM_CUDA(cudaEventElapsedTime(&t, m->prof_ev[2 * k], m->prof_ev[2 * k + 1]));
+    const int kind = m->prof_kind[k];
+    launches[kind] += 1;
+    ms[kind] += (double)t;
+  }
+  m->prof_used = 0;
+  return SLIM_OK;
 }
 
 slim_status slim_map_sync(slim_map* m, void* stream) {
@@ -354,16 +479,42 @@ slim_status slim_extract_tsdf(slim_map* m, int32_t* ijk_dev, float* D_dev, float
 
 extern "C" {
 
-slim_status slim_query(slim_map* m, const uint16_t*, int32_t, float, float, int32_t*, float*,
-                       float*, void*) {
+slim_status slim_query(slim_map* m, const uint16_t* q_dev, int32_t q, float temperature,
+                       float tp, int32_t* label_dev, float* prob_dev, float* scores_dev,
+                       void* stream) {
   if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
-  return fail(SLIM_ERR_UNSUPPORTED, "query not built yet");
+  if (m->mode != SLIM_OPEN) return fail(SLIM_ERR_UNSUPPORTED, "query needs an open-set map");
+  if (q < 1 || q > 256) return fail(SLIM_ERR_ARG, "q must be in [1, 256]");
+  if (!q_dev || (reinterpret_cast<uintptr_t>(q_dev) & 15))
+    return fail(SLIM_ERR_ARG, "q_dev must be non-NULL and 16-byte aligned");
+  if (!(temperature > 0.f) || !std::isfinite(temperature))
+    return fail(SLIM_ERR_ARG, "temperature must be finite and > 0");
+  if (!label_dev || !prob_dev) return fail(SLIM_ERR_ARG, "label/prob NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  slim_status s = read_counters(m, st);
+  if (s != SLIM_OK) return s;
+  if (m->pinned[kCtrStatus]) return status_of(m->pinned[kCtrStatus]);
+  const uint32_t rows = std::min<uint32_t>(m->pinned[kCtrRows], m->mv.row_cap);
+  return run_query(m, q_dev, q, temperature, tp, label_dev, prob_dev, scores_dev, rows, st);
 }
 
-slim_status slim_backward(slim_map* m, const float*, int64_t, const double*, const void*,
-                          const float*, const float*, const float*, float*, float*, void*) {
+slim_status slim_backward(slim_map* m, const float* pts_dev, int64_t n,
+                          const double pose_host[16], const void* sem_dev, const float* gD_dev,
+                          const float* gS_dev, const float* gB_dev, float* gsem_dev,
+                          float* gxyz_dev, void* stream) {
   if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
-  return fail(SLIM_ERR_UNSUPPORTED, "backward not built yet");
+  if (n < 0 || n > m->p.max_points) return fail(SLIM_ERR_ARG, "n must be in [0, max_points]");
+  if (!pose_host || !finite_pose(pose_host)) return fail(SLIM_ERR_ARG, "pose missing or not finite");
+  if (n > 0 && (!pts_dev || !sem_dev || !gD_dev || !gsem_dev || !gxyz_dev))
+    return fail(SLIM_ERR_ARG, "pts, sem, gD, gsem and gxyz are required");
+  if (n > 0 && m->mode != SLIM_CLOSED_ONEHOT && !gS_dev)
+    return fail(SLIM_ERR_ARG, "gS is required in the soft and open modes");
+  ScanGeom g;
+  compose_pose(pose_host, m->p.body_from_sensor, g, m->p.voxel_size, m->p.trunc,
+               m->p.min_range, m->p.max_range, m->cap);
+  return run_backward(m, g, pts_dev, static_cast<const float*>(sem_dev), n, gD_dev, gS_dev,
+                      m->mode == SLIM_OPEN ? gB_dev : nullptr, gsem_dev, gxyz_dev,
+                      (cudaStream_t)stream);
 }
 
 slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, void*) {

@@ -6,9 +6,9 @@
 namespace slim {
 
 constexpr uint64_t kEmptyKey = ~0ull;     // empty hash entry
-constexpr uint32_t kNoSlot = 0xFFFFFFFFu; // hash entry without a block slot
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu; // hash entry without a block slot (yet)
+constexpr uint32_t kFailSlot = 0xFFFFFFFEu; // block could not get a slot (capacity)
 constexpr int kBlockVoxels = 512;         // 8^3 voxels per block
-constexpr int kBucket = 32;               // hash bucket = one warp
 
 // Device counters held by each map.
 enum Counter : int {
@@ -34,10 +34,10 @@ __device__ __forceinline__ void raise_status(uint32_t* ctr, uint32_t code, uint3
 
 // Everything a kernel needs to reach one map's storage.
 struct MapView {
-  uint64_t* hkeys;      // [n_buckets * 32] block keys
-  uint32_t* hvals;      // [n_buckets * 32] block slots
-  uint32_t bucket_mask; // n_buckets - 1 (power of two)
-  int32_t max_probe;    // buckets probed before giving up
+  uint64_t* hkeys;      // [n_entries] block keys
+  uint32_t* hvals;      // [n_entries] block slots
+  uint32_t entry_mask;  // n_entries - 1 (power of two)
+  int32_t max_probe;    // entries probed before giving up
   uint64_t* blk_key;    // [block_cap] key of each allocated slot
   uint32_t block_cap;
   uint32_t* ctr;        // kNumCounters counters
@@ -49,6 +49,7 @@ struct MapView {
   float2* tsdf;         // [row_cap] (S = W*D, W)
   void* mrow;           // [row_cap * L] f32 or bf16 NIG mean
   void* brow;           // [row_cap * L] f32 or bf16 NIG beta
+  float* mnorm2;        // [row_cap] |m|^2 of the stored mean (query read-out)
   uint32_t row_cap;
 };
 
@@ -92,5 +93,15 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Longest time a kernel waits on another CTA before giving up (then it raises
+// kDevTimeout and skips the dependent work).
+constexpr uint64_t kCrossCtaWaitNs = 500ull * 1000 * 1000;
 
 }  // namespace slim

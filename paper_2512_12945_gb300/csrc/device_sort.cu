@@ -78,9 +78,11 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, voi
 }
 
 template <typename K>
-__global__ void __launch_bounds__(256) k_digit_hist(const K* __restrict__ keys, int64_t n,
-                                                    int shift, uint32_t* hist, int64_t ntiles) {
+__global__ void __launch_bounds__(256) k_digit_hist(const K* __restrict__ keys, int64_t n_max,
+                                                    const uint32_t* __restrict__ n_dev, int shift,
+                                                    uint32_t* hist, int64_t ntiles) {
   __shared__ uint32_t c[256];
+  const int64_t n = n_dev ? min(n_max, (int64_t)*n_dev) : n_max;
   c[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -96,10 +98,12 @@ __global__ void __launch_bounds__(256) k_digit_hist(const K* __restrict__ keys, 
 template <typename K>
 __global__ void __launch_bounds__(256) k_scatter(const K* __restrict__ kin,
                                                  const uint32_t* __restrict__ vin, K* kout,
-                                                 uint32_t* vout, int64_t n, int shift,
+                                                 uint32_t* vout, int64_t n_max,
+                                                 const uint32_t* __restrict__ n_dev, int shift,
                                                  const uint32_t* __restrict__ offs,
                                                  int64_t ntiles) {
   __shared__ uint32_t wh[256 * kCtaWarps];  // [digit][warp]
+  const int64_t n = n_dev ? min(n_max, (int64_t)*n_dev) : n_max;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const int64_t beg = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kWarpSpan;
   const int64_t end = min(n, beg + kWarpSpan);
@@ -155,7 +159,8 @@ size_t radix_sort_temp_bytes(int64_t n) {
 
 template <typename K>
 static cudaError_t radix_sort_impl(K* keys, uint32_t* vals, K* ktmp, uint32_t* vtmp, void* tmp,
-                                   int64_t n, int bits, cudaStream_t st) {
+                                   int64_t n, const uint32_t* n_dev, int bits,
+                                   cudaStream_t st) {
   if (n <= 1) return cudaSuccess;
   const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
   const int64_t nh = 256 * ntiles;
@@ -168,11 +173,12 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* vals, K* ktmp, uint32_t* v
   uint32_t* vb = vtmp;
   int passes = 0;
   for (int shift = 0; shift < bits; shift += 8, ++passes) {
-    k_digit_hist<K><<<(unsigned)ntiles, kCtaThreads, 0, st>>>(ka, n, shift, hist, ntiles);
+    k_digit_hist<K><<<(unsigned)ntiles, kCtaThreads, 0, st>>>(ka, n, n_dev, shift, hist,
+                                                               ntiles);
     cudaError_t e = exclusive_scan_u32(hist, offs, nh, partial, st);
     if (e != cudaSuccess) return e;
-    k_scatter<K><<<(unsigned)ntiles, kCtaThreads, 0, st>>>(ka, va, kb, vb, n, shift, offs,
-                                                          ntiles);
+    k_scatter<K><<<(unsigned)ntiles, kCtaThreads, 0, st>>>(ka, va, kb, vb, n, n_dev, shift,
+                                                          offs, ntiles);
     K* t = ka;
     ka = kb;
     kb = t;
@@ -180,7 +186,7 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* vals, K* ktmp, uint32_t* v
     va = vb;
     vb = tv;
   }
-  if (passes & 1) {
+  if (passes & 1) {  // the result is in the tmp buffers: copy back (bounded by n_max)
     cudaMemcpyAsync(keys, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
   }
@@ -190,13 +196,19 @@ static cudaError_t radix_sort_impl(K* keys, uint32_t* vals, K* ktmp, uint32_t* v
 cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp,
                            uint32_t* vals_tmp, void* tmp, int64_t n, int bits,
                            cudaStream_t st) {
-  return radix_sort_impl<uint64_t>(keys, vals, keys_tmp, vals_tmp, tmp, n, bits, st);
+  return radix_sort_impl<uint64_t>(keys, vals, keys_tmp, vals_tmp, tmp, n, nullptr, bits, st);
 }
 
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
                            uint32_t* vals_tmp, void* tmp, int64_t n, int bits,
                            cudaStream_t st) {
-  return radix_sort_impl<uint32_t>(keys, vals, keys_tmp, vals_tmp, tmp, n, bits, st);
+  return radix_sort_impl<uint32_t>(keys, vals, keys_tmp, vals_tmp, tmp, n, nullptr, bits, st);
+}
+
+cudaError_t radix_sort_u32_devn(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                                uint32_t* vals_tmp, void* tmp, int64_t n_max,
+                                const uint32_t* n_dev, int bits, cudaStream_t st) {
+  return radix_sort_impl<uint32_t>(keys, vals, keys_tmp, vals_tmp, tmp, n_max, n_dev, bits, st);
 }
 
 }  // namespace slim

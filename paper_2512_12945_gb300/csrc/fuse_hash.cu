@@ -1,0 +1,374 @@
+// Closed-set one-hot integration with shared-memory hash aggregation
+// (Sec. III-A TSDF + Sec. III-C / Theorem 1 Dirichlet counts), one kernel
+// per scan, one tile of TP points per CTA (TP = 64, 128 or 256 threads):
+//   1. every thread loads its point and class probabilities first (the
+//      probability row as independent float4 loads, argmax afterwards), then
+//      marches the band; each kept pair is added at once into a tile-local
+//      table keyed by (tile block entry, local voxel, class) holding
+//      (count, sum d) — no pair list is staged and nothing is sorted;
+//   2. each distinct block of the tile is inserted into (or found in) the
+//      map's hash by its own thread; blocks this CTA creates are zeroed by
+//      the whole CTA, then published; only then does the CTA wait
+//      (time-bounded) for blocks other CTAs are still publishing, so no wait
+//      can be part of a cycle;
+//   3. flush: S += sum d, W += count, c[class] += count per table entry
+//      (red.add; S = W D, see integrate_closed.cu).
+// A pair whose table probe runs out is re-generated after the slots are
+// known and sent to HBM on its own.
+#include "block_sort.cuh"
+#include "common.cuh"
+#include "geometry.cuh"
+#include "hash.cuh"
+#include "internal.h"
+
+namespace slim {
+
+constexpr uint32_t kVcEmpty = 0xFFFFFFFFu;
+
+template <int TP>
+struct HashTile {
+  static constexpr int kTbl = 8 * TP;    // block table entries (>= 2 x distinct blocks)
+  static constexpr int kVc = 16 * TP;    // (voxel, class) accumulators
+  static constexpr int kNew = 4 * TP;    // blocks a tile may create
+  static constexpr int kVcBits = kVc == 4096 ? 12 : (kVc == 2048 ? 11 : 10);
+  static constexpr size_t kSmem = (size_t)kTbl * 8 + (size_t)kTbl * 4 + (size_t)kVc * 12 +
+                                  (size_t)kNew * 2 + 16 * 4;
+};
+
+template <int TP>
+__device__ __forceinline__ uint32_t htbl_insert(uint64_t* tb, uint64_t kb) {
+  constexpr int N = HashTile<TP>::kTbl;
+  uint32_t h = (uint32_t)mix64(kb) & (N - 1);
+  for (int it = 0; it < N; ++it) {
+    const uint64_t cur = *(volatile uint64_t*)&tb[h];
+    if (cur == kb) return h;
+    if (cur == kEmptyKey) {
+      const unsigned long long prev = atomicCAS((unsigned long long*)&tb[h],
+                                                (unsigned long long)kEmptyKey,
+                                                (unsigned long long)kb);
+      if (prev == kEmptyKey || prev == kb) return h;
+    }
+    h = (h + 1) & (N - 1);
+  }
+  return 0xFFFFFFFFu;
+}
+
+template <int TP>
+__device__ __forceinline__ uint32_t htbl_find(const uint64_t* tb, uint64_t kb) {
+  constexpr int N = HashTile<TP>::kTbl;
+  uint32_t h = (uint32_t)mix64(kb) & (N - 1);
+  for (int it = 0; it < N; ++it) {
+    const uint64_t cur = tb[h];
+    if (cur == kb) return h;
+    if (cur == kEmptyKey) return 0xFFFFFFFFu;
+    h = (h + 1) & (N - 1);
+  }
+  return 0xFFFFFFFFu;
+}
+
+template <int TP>
+__device__ __forceinline__ int vc_insert(uint32_t* tbl, uint32_t key) {
+  constexpr int N = HashTile<TP>::kVc;
+  uint32_t h = (key * 2654435761u) >> (32 - HashTile<TP>::kVcBits);
+  for (int it = 0; it < 64; ++it) {
+    const uint32_t cur = *(volatile uint32_t*)&tbl[h];
+    if (cur == key) return (int)h;
+    if (cur == kVcEmpty) {
+      const uint32_t prev = atomicCAS(&tbl[h], kVcEmpty, key);
+      if (prev == kVcEmpty || prev == key) return (int)h;
+    }
+    h = (h + 1) & (N - 1);
+  }
+  return -1;
+}
+
+// Index of the largest of K probabilities (ties to the lowest index). The
+// loads of a group of 16 are issued together before any comparison.
+__device__ __forceinline__ uint32_t argmax_row(const float* __restrict__ row, int K) {
+  float bv = -INFINITY;
+  uint32_t best = 0;
+  if ((K & 3) == 0 && (reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    const int K4 = K >> 2;
+    for (int c = 0; c < K4; c += 4) {
+      float4 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        v[q] = (c + q < K4) ? __ldg(r4 + c + q) : make_float4(-INFINITY, -INFINITY, -INFINITY,
+                                                               -INFINITY);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = 4 * (c + q) + u;
+          if (k < K && (k == 0 || e[u] > bv)) {
+            bv = e[u];
+            best = (uint32_t)k;
+          }
+        }
+      }
+    }
+  } else {
+    for (int c = 0; c < K; c += 8) {
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (c + q < K) ? __ldg(row + c + q) : -INFINITY;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = c + q;
+        if (k < K && (k == 0 || v[q] > bv)) {
+          bv = v[q];
+          best = (uint32_t)k;
+        }
+      }
+    }
+  }
+  return best;
+}
+
+// One tile: points [tile * tile_points, (tile + 1) * tile_points) of a scan.
+template <int TP>
+__device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom& g,
+                                               const float* __restrict__ pts,
+                                               const float* __restrict__ sem, int64_t n, int K,
+                                               int tile_points, int64_t tile, unsigned char* sm) {
+  using H = HashTile<TP>;
+  uint64_t* tb_key = reinterpret_cast<uint64_t*>(sm);
+  uint32_t* tb_slot = reinterpret_cast<uint32_t*>(tb_key + H::kTbl);
+  uint32_t* vc_key = tb_slot + H::kTbl;
+  uint32_t* vc_cnt = vc_key + H::kVc;
+  float* vc_sum = reinterpret_cast<float*>(vc_cnt + H::kVc);
+  uint16_t* newe = reinterpret_cast<uint16_t*>(vc_sum + H::kVc);
+  uint32_t* misc = reinterpret_cast<uint32_t*>(newe + H::kNew);
+
+  const int tid = threadIdx.x;
+  // loads first: the point and its class probabilities
+  const int64_t j = tile * tile_points + tid;
+  const bool mine = tid < tile_points && j < n;
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f;
+  uint32_t cls = 0;
+  if (mine) {
+    p0 = __ldg(pts + 3 * j);
+    p1 = __ldg(pts + 3 * j + 1);
+    p2 = __ldg(pts + 3 * j + 2);
+    cls = argmax_row(sem + (size_t)j * K, K);
+  }
+  if (tid == 0) {
+    misc[0] = *(volatile uint32_t*)&mv.ctr[kCtrStatus];
+    misc[1] = 0;
+    misc[2] = 0;
+  }
+  for (int e = tid; e < H::kTbl; e += TP) tb_key[e] = kEmptyKey;
+  for (int e = tid; e < H::kVc / 4; e += TP) {
+    reinterpret_cast<uint4*>(vc_key)[e] = make_uint4(kVcEmpty, kVcEmpty, kVcEmpty, kVcEmpty);
+    reinterpret_cast<uint4*>(vc_cnt)[e] = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<float4*>(vc_sum)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  if (misc[0]) return;
+
+  // 1. band DDA, aggregating every pair into the (voxel, class) table
+  int ovf = -1;  // index of the first pair the table could not take
+  Ray ry;
+  const bool valid = mine && ray_setup(g, p0, p1, p2, ry);
+  if (valid) {
+    Ray r2 = ry;
+    uint64_t last = kEmptyKey;
+    uint32_t last_tb = 0;
+    int k = 0;
+    ray_for_each(g, r2, [&](int32_t i0, int32_t i1, int32_t i2, float d) {
+      const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
+      if (kb != last) {
+        last = kb;
+        last_tb = htbl_insert<TP>(tb_key, kb);
+        if (last_tb == 0xFFFFFFFFu) misc[2] = 1;
+      }
+      const int idx = k++;
+      if (last_tb == 0xFFFFFFFFu || ovf >= 0) return;
+      const uint32_t key = (last_tb << 15) | ((uint32_t)local_index(i0, i1, i2) << 6) | cls;
+      const int e = vc_insert<TP>(vc_key, key);
+      if (e < 0) {
+        ovf = idx;
+        return;
+      }
+      atomicAdd(&vc_cnt[e], 1u);
+      atomicAdd(&vc_sum[e], d);
+    });
+  }
+  __syncthreads();
+  if (misc[2]) {
+    if (tid == 0) raise_status(mv.ctr, kDevInternal, 4);
+    return;
+  }
+
+  // 2. insert-or-find each distinct block (table entries tid + TP q)
+  constexpr int Q = H::kTbl / TP;
+  uint32_t hpos[Q];
+  uint32_t created = 0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int e = tid + q * TP;
+    const uint64_t key = tb_key[e];
+    hpos[q] = 0;
+    if (key == kEmptyKey) continue;
+    uint32_t h = entry_of(mv, key);
+    int state = -1;
+    for (int pr = 0; pr < mv.max_probe; ++pr) {
+      const uint64_t cur = *(volatile uint64_t*)&mv.hkeys[h];
+      if (cur == key) {
+        state = 0;
+        break;
+      }
+      if (cur == kEmptyKey) {
+        const unsigned long long prev =
+            atomicCAS((unsigned long long*)&mv.hkeys[h], (unsigned long long)kEmptyKey,
+                      (unsigned long long)key);
+        if (prev == kEmptyKey) {
+          state = 1;
+          break;
+        }
+        if (prev == key) {
+          state = 0;
+          break;
+        }
+      }
+      h = (h + 1) & mv.entry_mask;
+    }
+    hpos[q] = h;
+    if (state < 0) {
+      raise_status(mv.ctr, kDevCapacity, 2);
+      tb_slot[e] = kFailSlot;
+    } else if (state == 1) {
+      const uint32_t slot = atomicAdd(&mv.ctr[kCtrBlocks], 1u);
+      const uint32_t ni = slot < mv.block_cap ? atomicAdd(&misc[1], 1u) : 0u;
+      if (slot >= mv.block_cap || ni >= (uint32_t)H::kNew) {
+        raise_status(mv.ctr, slot >= mv.block_cap ? kDevCapacity : kDevInternal, 1);
+        *(volatile uint32_t*)&mv.hvals[h] = kFailSlot;
+        tb_slot[e] = kFailSlot;
+      } else {
+        mv.blk_key[slot] = key;
+        tb_slot[e] = slot;
+        newe[ni] = (uint16_t)e;
+        created |= 1u << q;
+      }
+    } else {
+      tb_slot[e] = kNoSlot;
+    }
+  }
+  __syncthreads();
+  const uint32_t nnew = min(misc[1], (uint32_t)H::kNew);
+  for (uint32_t i = 0; i < nnew; ++i) {
+    float4* p = reinterpret_cast<float4*>(mv.rec + (size_t)tb_slot[newe[i]] * kBlockVoxels * mv.rs);
+    const int n4 = kBlockVoxels * mv.rs / 4;
+    for (int k = tid; k < n4; k += TP) p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __threadfence();
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    if (created & (1u << q)) *(volatile uint32_t*)&mv.hvals[hpos[q]] = tb_slot[tid + q * TP];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int e = tid + q * TP;
+    if (tb_key[e] == kEmptyKey || tb_slot[e] != kNoSlot) continue;
+    volatile uint32_t* hv = &mv.hvals[hpos[q]];
+    uint32_t v = *hv;
+    if (v == kNoSlot) {
+      const uint64_t t0 = global_ns();
+      while ((v = *hv) == kNoSlot) {
+        if (global_ns() - t0 > kCrossCtaWaitNs) {
+          raise_status(mv.ctr, kDevTimeout, 5);
+          v = kFailSlot;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    tb_slot[e] = v;
+  }
+  __threadfence();
+  __syncthreads();
+
+  // 3. flush: one red.add each for S, W and the class count per entry
+  for (int e = tid; e < H::kVc; e += TP) {
+    const uint32_t key = vc_key[e];
+    if (key == kVcEmpty) continue;
+    const uint32_t slot = tb_slot[key >> 15];
+    if (slot >= kFailSlot) continue;
+    float* r = mv.rec + ((size_t)slot * kBlockVoxels + ((key >> 6) & 511u)) * mv.rs;
+    const float c = (float)vc_cnt[e];
+    atomicAdd(r, vc_sum[e]);
+    atomicAdd(r + 1, c);
+    atomicAdd(r + 2 + (key & 63u), c);
+  }
+
+  // 4. pairs the table could not take go to HBM one by one
+  if (valid && ovf >= 0) {
+    uint64_t last = kEmptyKey;
+    uint32_t slot = kFailSlot;
+    int k = 0;
+    ray_for_each(g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d) {
+      const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
+      if (kb != last) {
+        last = kb;
+        const uint32_t te = htbl_find<TP>(tb_key, kb);
+        slot = te == 0xFFFFFFFFu ? kFailSlot : tb_slot[te];
+      }
+      if (k++ < ovf || slot >= kFailSlot) return;
+      float* r = mv.rec + ((size_t)slot * kBlockVoxels + local_index(i0, i1, i2)) * mv.rs;
+      atomicAdd(r, d);
+      atomicAdd(r + 1, 1.f);
+      atomicAdd(r + 2 + cls, 1.f);
+    });
+  }
+}
+
+template <int TP>
+__global__ void __launch_bounds__(TP) k_fuse_hash(MapView mv, ScanGeom g,
+                                                  const float* __restrict__ pts,
+                                                  const float* __restrict__ sem, int64_t n, int K,
+                                                  int tile_points) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  fuse_hash_tile<TP>(mv, g, pts, sem, n, K, tile_points, blockIdx.x, sm);
+}
+
+cudaError_t hash_setup_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_fuse_hash<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)HashTile<64>::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fuse_hash<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)HashTile<128>::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fuse_hash<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)HashTile<256>::kSmem);
+  return e;
+}
+
+// Largest number of points a TP-thread tile may hold: its distinct blocks
+// (at most points x band_blocks) must fit the block table at half load.
+int hash_tile_points(int TP, int band_blocks) {
+  int tp = TP;
+  while (tp > 16 && tp * band_blocks > 4 * TP) tp >>= 1;
+  return tp;
+}
+
+int hash_max_tile(int band_blocks) { return hash_tile_points(256, band_blocks); }
+
+cudaError_t launch_fuse_hash(const MapView& mv, const ScanGeom& g, const float* pts,
+                             const float* sem, int64_t n, int K, int tile, int band_blocks,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int TP = tile <= 64 ? 64 : (tile <= 128 ? 128 : 256);
+  const int tp = hash_tile_points(TP, band_blocks);
+  const unsigned grid = (unsigned)((n + tp - 1) / tp);
+  if (TP == 64)
+    k_fuse_hash<64><<<grid, 64, HashTile<64>::kSmem, st>>>(mv, g, pts, sem, n, K, tp);
+  else if (TP == 128)
+    k_fuse_hash<128><<<grid, 128, HashTile<128>::kSmem, st>>>(mv, g, pts, sem, n, K, tp);
+  else
+    k_fuse_hash<256><<<grid, 256, HashTile<256>::kSmem, st>>>(mv, g, pts, sem, n, K, tp);
+  return cudaGetLastError();
+}
+
+}  // namespace slim

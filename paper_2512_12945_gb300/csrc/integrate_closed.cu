@@ -1,19 +1,19 @@
 // Closed-set scan integration (Sec. III-A TSDF + Sec. III-C Dirichlet counts).
 //
-// Two kernels per scan:
-//   k_traverse_alloc  one thread per point: validity, transform, band DDA
-//                     (SDF filter included, so only blocks with a kept
-//                     observation are created), then the warp's distinct
-//                     blocks are inserted into the hash cooperatively and
-//                     new blocks are zero-initialised by the inserting warp.
-//   k_fuse_closed     one 256-point tile per CTA: the DDA is re-run, every
-//                     (voxel, point) pair goes to shared memory as
-//                     (tile block, local voxel, d), the tile's distinct
-//                     blocks are looked up once, the pairs are sorted by
-//                     voxel key (stable CTA radix sort) and reduced per voxel
-//                     segment with warp shuffles; one red.add per voxel (and
-//                     per present class) goes to HBM instead of one atomic
-//                     per pair.
+// One kernel per scan, k_fuse_closed, one 256-point tile per CTA:
+//   1. band DDA per point; every kept (voxel, point) pair goes to shared
+//      memory as (tile block, local voxel, d), pair k of point t at k * 256 + t
+//      (bank-conflict free); the tile's distinct blocks go to a shared table;
+//   2. each distinct block is inserted into (or found in) the map's hash by
+//      its own thread; blocks this CTA creates are zeroed by the whole CTA and
+//      then published, and only then does the CTA wait (time-bounded) for
+//      blocks other CTAs are still publishing — every CTA publishes before it
+//      waits, so no wait can be part of a cycle;
+//   3. the pairs are sorted by voxel key (stable CTA radix sort) and reduced
+//      per voxel run with warp shuffles; one red.add per voxel (and per
+//      present class) goes to HBM instead of one atomic per pair.
+// k_traverse_alloc (the block-allocation pass on its own) serves the
+// open-set path, whose pair pass needs every slot published beforehand.
 //
 // Voxel record (AoS, rs floats, 16-byte aligned): {S, W, c_0 .. c_{K-1}, pad}
 // with S = W * D. With w~ = 1 the paper's running average
@@ -75,17 +75,34 @@ __global__ void __launch_bounds__(256) k_traverse_alloc(MapView mv, ScanGeom g,
     raise_status(mv.ctr, kDevInternal, 3);
     cnt = kMaxBandBlocks;
   }
+  // per round: drop duplicate keys in the warp, the leaders insert in
+  // parallel, then the warp zeroes each new block and publishes its slot
+  const unsigned lane = lane_id();
   const int maxc = __reduce_max_sync(0xFFFFFFFFu, cnt);
   for (int r = 0; r < maxc; ++r) {
     const bool has = r < cnt;
-    const uint64_t key = has ? kbuf[threadIdx.x][r] : 0ull;
-    unsigned pending = __ballot_sync(0xFFFFFFFFu, has);
-    while (pending) {
-      const int src = __ffs(pending) - 1;
-      const uint64_t k = __shfl_sync(0xFFFFFFFFu, key, src);
-      pending &= ~__ballot_sync(0xFFFFFFFFu, has && key == k);
-      warp_insert(mv, k, [&](uint32_t slot) { zero_block(mv, slot, open != 0); });
+    const uint64_t key = has ? kbuf[threadIdx.x][r] : kEmptyKey;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, (unsigned long long)key);
+    const bool leader = has && (int)lane == __ffs(peers) - 1;
+    const int64_t h = leader ? hash_insert(mv, key) : -1;
+    uint32_t slot = kNoSlot;
+    if (h >= 0) {
+      slot = atomicAdd(&mv.ctr[kCtrBlocks], 1u);
+      if (slot >= mv.block_cap) {
+        raise_status(mv.ctr, kDevCapacity, 1);
+        slot = kNoSlot;
+      } else {
+        mv.blk_key[slot] = key;
+      }
     }
+    unsigned nm = __ballot_sync(0xFFFFFFFFu, slot != kNoSlot);
+    while (nm) {
+      const int src = __ffs(nm) - 1;
+      zero_block(mv, __shfl_sync(0xFFFFFFFFu, slot, src), open != 0);
+      nm &= nm - 1;
+    }
+    __syncwarp();
+    if (slot != kNoSlot) mv.hvals[h] = slot;
   }
 }
 
@@ -141,9 +158,9 @@ __global__ void __launch_bounds__(256, 2)
   __syncthreads();
   if (misc[0]) return;
 
-  // 1. band DDA: raw pairs at [tid * cap, tid * cap + np)
+  // 1. band DDA: pair k of this thread's point at raw index k * tile + tid
   const int64_t j = (int64_t)blockIdx.x * tile_points + tid;
-  const int base = tid * g.cap;
+  const int tp_shift = 31 - __clz(tile_points);  // tile_points is a power of two
   int np = 0;
   uint8_t mycls = 0;
   if (tid < tile_points && j < n) {
@@ -174,8 +191,9 @@ __global__ void __launch_bounds__(256, 2)
           if (last_tb == 0xFFFFFFFFu) misc[2] = 1;
         }
         if (last_tb != 0xFFFFFFFFu) {
-          sB[base + np] = (last_tb << 9) | (uint32_t)local_index(i0, i1, i2);
-          pd[base + np] = d;
+          const int raw = (np << tp_shift) + tid;
+          sB[raw] = (last_tb << 9) | (uint32_t)local_index(i0, i1, i2);
+          pd[raw] = d;
           ++np;
         }
       });
@@ -185,7 +203,9 @@ __global__ void __launch_bounds__(256, 2)
   __syncthreads();
 
   // 2. dense ids for the tile's blocks (8 table entries per thread)
-  uint64_t* dkey = reinterpret_cast<uint64_t*>(sA);  // dense id -> key (scratch)
+  uint64_t* dkey = reinterpret_cast<uint64_t*>(sA);      // dense id -> key
+  uint32_t* dent = reinterpret_cast<uint32_t*>(sA) + 2 * kMaxTileBlocks;  // hash entry
+  uint32_t* dnew = dent + kMaxTileBlocks;                // ids of blocks created here
   {
     uint32_t occ = 0;
 #pragma unroll
@@ -202,7 +222,10 @@ __global__ void __launch_bounds__(256, 2)
         ++off;
       }
     }
-    if (tid == 0) misc[1] = nb;
+    if (tid == 0) {
+      misc[1] = nb;
+      misc[3] = 0;
+    }
   }
   uint32_t npairs;
   const uint32_t poff = cta_exclusive_scan((uint32_t)np, wtot, &npairs);
@@ -213,16 +236,89 @@ __global__ void __launch_bounds__(256, 2)
     return;
   }
 
-  // 3. one hash lookup per distinct block of the tile
-  for (uint32_t dd = warp; dd < nb; dd += kCtaWarps) {
-    const uint32_t s = warp_find(mv, dkey[dd]);
-    if (lane == 0) tb_slot[dd] = s;
+  // 3. insert-or-find every distinct block (one thread each)
+  for (uint32_t dd = tid; dd < nb; dd += kCtaThreads) {
+    const uint64_t key = dkey[dd];
+    uint32_t h = entry_of(mv, key);
+    int state = -1;  // 0 found, 1 created here
+    for (int pr = 0; pr < mv.max_probe; ++pr) {
+      const uint64_t cur = *(volatile uint64_t*)&mv.hkeys[h];
+      if (cur == key) {
+        state = 0;
+        break;
+      }
+      if (cur == kEmptyKey) {
+        const unsigned long long prev =
+            atomicCAS((unsigned long long*)&mv.hkeys[h], (unsigned long long)kEmptyKey,
+                      (unsigned long long)key);
+        if (prev == kEmptyKey) {
+          state = 1;
+          break;
+        }
+        if (prev == key) {
+          state = 0;
+          break;
+        }
+      }
+      h = (h + 1) & mv.entry_mask;
+    }
+    dent[dd] = h;
+    if (state < 0) {
+      raise_status(mv.ctr, kDevCapacity, 2);
+      tb_slot[dd] = kFailSlot;
+    } else if (state == 1) {
+      const uint32_t slot = atomicAdd(&mv.ctr[kCtrBlocks], 1u);
+      if (slot >= mv.block_cap) {
+        raise_status(mv.ctr, kDevCapacity, 1);
+        *(volatile uint32_t*)&mv.hvals[h] = kFailSlot;
+        tb_slot[dd] = kFailSlot;
+      } else {
+        mv.blk_key[slot] = key;
+        tb_slot[dd] = slot;
+        dnew[atomicAdd(&misc[3], 1u)] = dd;
+      }
+    } else {
+      tb_slot[dd] = kNoSlot;  // resolved below
+    }
   }
+  __syncthreads();
+  // zero the blocks created by this CTA, then publish their slots
+  const uint32_t nnew = misc[3];
+  for (uint32_t i = 0; i < nnew; ++i) {
+    float4* p = reinterpret_cast<float4*>(mv.rec + (size_t)tb_slot[dnew[i]] * kBlockVoxels * mv.rs);
+    const int n4 = kBlockVoxels * mv.rs / 4;
+    for (int k = tid; k < n4; k += kCtaThreads) p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __threadfence();
+  __syncthreads();
+  for (uint32_t i = tid; i < nnew; i += kCtaThreads) {
+    const uint32_t dd = dnew[i];
+    *(volatile uint32_t*)&mv.hvals[dent[dd]] = tb_slot[dd];
+  }
+  // wait for blocks other CTAs created and have not yet published
+  for (uint32_t dd = tid; dd < nb; dd += kCtaThreads) {
+    if (tb_slot[dd] != kNoSlot) continue;
+    volatile uint32_t* hv = &mv.hvals[dent[dd]];
+    uint32_t v = *hv;
+    if (v == kNoSlot) {
+      const uint64_t t0 = global_ns();
+      while ((v = *hv) == kNoSlot) {
+        if (global_ns() - t0 > kCrossCtaWaitNs) {
+          raise_status(mv.ctr, kDevTimeout, 5);
+          v = kFailSlot;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    tb_slot[dd] = v;
+  }
+  __threadfence();
   __syncthreads();
 
   // 4. sort keys: ((dense block << 9 | local) << 13) | raw pair index
   for (int k = 0; k < np; ++k) {
-    const uint32_t raw = (uint32_t)(base + k);
+    const uint32_t raw = (uint32_t)((k << tp_shift) + tid);
     const uint32_t w = sB[raw];
     const uint32_t key2 = ((uint32_t)tb_dense[w >> 9] << 9) | (w & 511u);
     sA[poff + k] = (key2 << 13) | raw;
@@ -239,7 +335,7 @@ __global__ void __launch_bounds__(256, 2)
     const uint32_t c = act ? sorted[i] : 0u;
     const uint32_t key2 = act ? (c >> 13) : 0xFFFFFFFFu;
     const uint32_t raw = c & 0x1FFFu;
-    const int pt = act ? (int)(raw / (uint32_t)g.cap) : 0;
+    const int pt = act ? (int)(raw & (uint32_t)(tile_points - 1)) : 0;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, key2);
     const int first = __ffs(peers) - 1, lastl = 31 - __clz(peers);
     float dsum = act ? pd[raw] : 0.f;
@@ -254,7 +350,7 @@ __global__ void __launch_bounds__(256, 2)
       }
     }
     const uint32_t slot = act ? tb_slot[key2 >> 9] : kNoSlot;
-    float* r = (slot != kNoSlot) ? mv.rec + ((size_t)slot * kBlockVoxels + (key2 & 511u)) * mv.rs
+    float* r = (slot < kFailSlot) ? mv.rec + ((size_t)slot * kBlockVoxels + (key2 & 511u)) * mv.rs
                                  : nullptr;
     if (r && (int)lane == first) {
       atomicAdd(r, dsum);
@@ -290,6 +386,8 @@ cudaError_t launch_traverse_alloc(const MapView& mv, const ScanGeom& g, const fl
 
 cudaError_t closed_setup_attributes(int mode, int K, int tile_points) {
   const size_t sm = closed_smem_bytes(mode, K, tile_points);
+  cudaError_t e = hash_setup_attributes();
+  if (e != cudaSuccess) return e;
   if (mode == 0)
     return cudaFuncSetAttribute(k_fuse_closed<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sm);
@@ -298,9 +396,8 @@ cudaError_t closed_setup_attributes(int mode, int K, int tile_points) {
 }
 
 int closed_tile_points(int cap, int band_blocks) {
-  int tp = 256;
-  tp = min(tp, (kTileCap / cap) & ~31);
-  tp = min(tp, (kMaxTileBlocks / band_blocks) & ~31);
+  int tp = 256;  // a power of two: the pair layout shifts by log2(tp)
+  while (tp > 32 && (tp * cap > kTileCap || tp * band_blocks > kMaxTileBlocks)) tp >>= 1;
   return tp;
 }
 

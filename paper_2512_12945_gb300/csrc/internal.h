@@ -16,6 +16,12 @@ cudaError_t launch_fuse_closed(const MapView& mv, const ScanGeom& g, const float
                                const float* sem, int64_t n, int mode, int K, int tile_points,
                                cudaStream_t st);
 cudaError_t closed_setup_attributes(int mode, int K, int tile_points);
+// fuse_hash.cu: one-hot hash aggregation; tile = points per CTA (64, 128 or 256)
+cudaError_t hash_setup_attributes();
+cudaError_t launch_fuse_hash(const MapView& mv, const ScanGeom& g, const float* pts,
+                             const float* sem, int64_t n, int K, int tile, int band_blocks,
+                             cudaStream_t st);
+int hash_max_tile(int band_blocks);
 int closed_tile_points(int cap, int band_blocks);
 int max_band_blocks();
 
@@ -29,6 +35,11 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_tmp,
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
                            uint32_t* vals_tmp, void* tmp, int64_t n, int bits,
                            cudaStream_t st);
+// As radix_sort_u32 with the item count read on the device from *n_dev
+// (at most n_max items; the launch is sized for n_max).
+cudaError_t radix_sort_u32_devn(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                                uint32_t* vals_tmp, void* tmp, int64_t n_max,
+                                const uint32_t* n_dev, int bits, cudaStream_t st);
 // Exclusive scan of n uint32 counts into out (n + 1 entries, out[n] = total).
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp,
                                cudaStream_t st);

@@ -1,5 +1,6 @@
 // The map handle behind the C ABI, shared by the host-side translation units.
 #pragma once
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -11,16 +12,22 @@ slim_status fail(slim_status s, const std::string& msg);
 
 // Scratch of the open-set path, sized by max_points at map creation.
 struct OpenScratch {
-  int64_t pair_cap = 0;     // (voxel, point) pairs per scan
-  uint32_t* keys = nullptr; // voxel key per pair (slot << 9 | local)
-  uint32_t* vals = nullptr; // pair index -> (point << 5 | step)
-  uint32_t* keys_tmp = nullptr;
+  int64_t pair_cap = 0;          // (voxel, point) pairs per scan
+  uint32_t* keys = nullptr;      // voxel key per pair (slot << 9 | local)
+  uint32_t* vals = nullptr;      // pair index, permuted with the keys
+  uint32_t* keys_tmp = nullptr;  // sort ping-pong buffers
   uint32_t* vals_tmp = nullptr;
-  float* pair_d = nullptr;  // d per pair, by pair index
-  uint32_t* npairs = nullptr;  // device counter
-  uint32_t* seg_flag = nullptr;  // segment heads
-  uint32_t* seg_off = nullptr;   // segment starts (scan of heads)
-  void* tmp = nullptr;      // sort / scan temp
+  float* pair_d = nullptr;       // SDF of each pair, by pair index
+  uint32_t* pair_pt = nullptr;   // point of each pair, by pair index
+  uint32_t* seg_start = nullptr; // first sorted position of each voxel run
+  uint32_t* ctr = nullptr;       // device counters: pairs, runs
+  void* tmp = nullptr;           // sort / scan temp
+};
+// Scratch of the open-set query.
+struct QueryScratch {
+  void* abf = nullptr;     // FP32 storage: BF16 copy of the means [row_cap x L]
+  float* rnorm2 = nullptr; // FP32 storage: |m|^2 of the BF16 copy [row_cap]
+  float* qinv = nullptr;   // [256] 1 / |q|
 };
 }  // namespace slim
 
@@ -29,7 +36,8 @@ struct slim_map {
   int device = 0;
   int K = 0, L = 0, mode = 0, bf16 = 0, rs = 0;
   int cap = 0, band_blocks = 0, tile_points = 0;
-  uint32_t n_buckets = 0;
+  int hash_tile = 256;  // threads (points) per CTA of the hash-aggregation kernel
+  uint64_t n_entries = 0;
   slim::MapView mv{};
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -45,6 +53,12 @@ struct slim_map {
   void* ex_tmp = nullptr;
   uint32_t* pinned = nullptr;  // host copy of the device counters
   slim::OpenScratch open{};
+  slim::QueryScratch qscratch{};
+  // kernel timing (slim_profile_enable)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;  // pairs: [2k] start, [2k+1] end
+  std::vector<int> prof_kind;
+  size_t prof_used = 0;
   int64_t scans = 0;
 
   template <class T>
@@ -67,6 +81,8 @@ struct slim_map {
     return SLIM_OK;
   }
   void release() {
+    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+    prof_ev.clear();
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
     if (pinned) cudaFreeHost(pinned);
@@ -76,8 +92,19 @@ struct slim_map {
 
 
 namespace slim {
+// Bracket one kernel launch with timing events when profiling is on.
+// prof_begin returns a token for prof_end (-1 when off).
+int prof_begin(slim_map* m, int kind, cudaStream_t st);
+void prof_end(slim_map* m, int token, cudaStream_t st);
 slim_status open_alloc_scratch(slim_map* m, OpenScratch& o, int64_t max_points);
 cudaError_t open_setup_attributes(slim_map* m);
+cudaError_t query_setup_attributes();
+slim_status run_backward(slim_map* m, const ScanGeom& g, const float* pts, const float* sem,
+                         int64_t n, const float* gD, const float* gS, const float* gB,
+                         float* gsem, float* gxyz, cudaStream_t st);
+slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float temperature, float tp,
+                      int32_t* label, float* prob, float* scores, uint32_t n_rows,
+                      cudaStream_t st);
 slim_status open_integrate(slim_map* m, const MapView& mv, OpenScratch& o, const ScanGeom& g,
                            const float* pts, const float* sem, int64_t n, int L, int bf16,
                            cudaStream_t st);

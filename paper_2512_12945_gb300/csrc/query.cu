@@ -1,0 +1,469 @@
+// Open-set read-out (end of Sec. III-D, Fig. "sit"): cosine similarity of
+// every voxel's NIG mean m against Q query embeddings, softmax over the
+// queries of cos / T, most probable query kept when its probability reaches
+// T_p. The scores are one dense contraction S = M Q^T (voxels x l times
+// l x queries), run on the 5th-generation tensor cores:
+//
+//   warp 0      one thread issues TMA loads (128B swizzle) of a 128 x 64 tile
+//               of M and the N x 64 tile of the queries per stage into a
+//               4-stage shared-memory ring;
+//   warp 1      one thread issues tcgen05.mma (kind::f16, BF16 in, FP32
+//               accumulate, M = 128, N = queries rounded up to 16) into one of
+//               two TMEM accumulators, and tcgen05.commit frees each stage;
+//   warps 2-5   epilogue: tcgen05.ld of the accumulator rows (one voxel per
+//               thread), cosine = dot / (|m| |q|), online softmax, argmax,
+//               threshold; the accumulator is released for the next tile.
+//
+// The grid is persistent (one CTA per SM, tiles strided over CTAs). Every
+// mbarrier wait is bounded: running out raises the map status, the CTA stops
+// issuing work, waits (bounded) for its own copies and MMAs and frees TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "map.h"
+
+namespace slim {
+
+constexpr int kQM = 128;        // voxel rows per tile
+constexpr int kQK = 64;         // K elements per stage (128-byte rows)
+constexpr int kQStages = 4;
+constexpr int kQThreads = 192;  // 6 warps
+constexpr uint64_t kWaitNs = 500ull * 1000 * 1000;  // a wait gives up after 0.5 s
+
+struct QueryArgs {
+  uint32_t n_rows;
+  int32_t L;
+  int32_t Q;
+  int32_t N;         // Q rounded up to 16
+  uint32_t tmem_cols;
+  float inv_temp;
+  float tp;
+  const float* qinv;    // [Q] 1 / |q|
+  const float* rnorm2;  // [n_rows] |m|^2
+  int32_t* label;
+  float* prob;
+  float* scores;        // [n_rows x Q] cosines or null
+  uint32_t* status;     // map counters (sticky status)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false when kWaitNs of wall time ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 15) == 0 && global_ns() - t0 > kWaitNs) return false;
+    if (it > 64) __nanosleep(64);
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x,
+                                            int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// K-major operand, 128-byte swizzle: rows of 128 B, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kQThreads, 1)
+    k_query(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            QueryArgs a) {
+  extern __shared__ unsigned char q_smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(q_smem_raw) + 1023) & ~(uintptr_t)1023);
+  const uint32_t bytesA = kQM * 128;
+  const uint32_t bytesB = (uint32_t)a.N * 128;
+  unsigned char* sA = sm;
+  unsigned char* sB = sA + kQStages * bytesA;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kQStages * bytesB);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kQStages;
+  uint64_t* tfull = bars + 2 * kQStages;
+  uint64_t* tempty = bars + 2 * kQStages + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kQStages + 4);
+  volatile uint32_t* abort_flag = tmem_slot + 1;
+  float* s_qinv = reinterpret_cast<float*>(tmem_slot + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t num_tiles = (a.n_rows + kQM - 1) / kQM;
+  const int kchunks = a.L / kQK;
+
+  for (int c = threadIdx.x; c < a.N; c += kQThreads) s_qinv[c] = c < a.Q ? a.qinv[c] : 0.f;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kQStages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(smem_u32(&tfull[s]), 1);
+      mbar_init(smem_u32(&tempty[s]), 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t issued = 0;
+    int last_stage[kQStages];
+    uint32_t last_phase[kQStages];
+    for (uint32_t tile = blockIdx.x; tile < num_tiles && !*abort_flag; tile += gridDim.x) {
+      for (int kc = 0; kc < kchunks; ++kc) {
+        if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1)) {
+          *abort_flag = 1;
+          raise_status(a.status, kDevTimeout, 20);
+          break;
+        }
+        const uint32_t fb = smem_u32(&full[stage]);
+        mbar_expect_tx(fb, bytesA + bytesB);
+        tma_load_2d(smem_u32(sA + stage * bytesA), &tmA, kc * kQK, (int32_t)(tile * kQM), fb);
+        tma_load_2d(smem_u32(sB + stage * bytesB), &tmB, kc * kQK, 0, fb);
+        last_stage[issued % kQStages] = stage;
+        last_phase[issued % kQStages] = phase;
+        ++issued;
+        if (++stage == kQStages) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+    // every issued copy has landed before the CTA may exit
+    const uint32_t tail = issued < (uint32_t)kQStages ? issued : (uint32_t)kQStages;
+    for (uint32_t i = 0; i < tail; ++i) {
+      const uint32_t k = (issued - 1 - i) % kQStages;
+      mbar_wait(smem_u32(&full[last_stage[k]]), last_phase[k]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ----------------------------------------------------------------- MMA
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.N >> 3) << 17) |
+                           ((uint32_t)(kQM >> 4) << 24);
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    bool committed_any = false;
+    uint32_t last_commit_bar = 0, last_commit_phase = 0;
+    for (uint32_t tile = blockIdx.x; tile < num_tiles && !*abort_flag; tile += gridDim.x) {
+      if (!mbar_wait(smem_u32(&tempty[acc]), acc_phase ^ 1)) {
+        *abort_flag = 1;
+        raise_status(a.status, kDevTimeout, 21);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + (uint32_t)(acc * a.N);
+      bool ok = true;
+      for (int kc = 0; kc < kchunks; ++kc) {
+        if (!mbar_wait(smem_u32(&full[stage]), phase)) {
+          *abort_flag = 1;
+          raise_status(a.status, kDevTimeout, 22);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA + stage * bytesA);
+        const uint32_t b0 = smem_u32(sB + stage * bytesB);
+#pragma unroll
+        for (int k = 0; k < kQK / 16; ++k)
+          mma_bf16(d_tmem, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32), idesc,
+                   (kc > 0 || k > 0) ? 1u : 0u);
+        mma_commit(smem_u32(&empty[stage]));
+        if (++stage == kQStages) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (!ok) break;
+      mma_commit(smem_u32(&tfull[acc]));
+      committed_any = true;
+      last_commit_bar = smem_u32(&tfull[acc]);
+      last_commit_phase = acc_phase;
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1;
+      }
+    }
+    // the MMAs must be complete before TMEM is freed
+    if (committed_any) mbar_wait(last_commit_bar, last_commit_phase);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int quarter = warp & 3;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+      bool ok = mbar_wait(smem_u32(&tfull[acc]), acc_phase);
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      if (!ok || *abort_flag) {
+        if (lane == 0) {
+          *abort_flag = 1;
+          raise_status(a.status, kDevTimeout, 23);
+        }
+        break;
+      }
+      tc_fence_after();
+      const uint32_t row = tile * kQM + quarter * 32 + lane;
+      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * a.N);
+      const float n2 = row < a.n_rows ? a.rnorm2[row] : 0.f;
+      const float rinv = n2 > 0.f ? rsqrtf(n2) : 0.f;
+      const float sc = rinv * a.inv_temp;
+      float mrun = -INFINITY, srun = 0.f;
+      int best = -1;
+      for (int c0 = 0; c0 < a.N; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(taddr + (uint32_t)c0, r);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = c0 + j;
+          if (c >= a.Q) break;
+          const float cosv = __uint_as_float(r[j]) * s_qinv[c] * rinv;
+          if (a.scores && row < a.n_rows) a.scores[(size_t)row * a.Q + c] = cosv;
+          const float x = cosv * a.inv_temp;
+          if (x > mrun) {
+            srun = srun * __expf(mrun - x) + 1.f;
+            mrun = x;
+            best = c;
+          } else {
+            srun += __expf(x - mrun);
+          }
+        }
+      }
+      (void)sc;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
+      if (row < a.n_rows) {
+        if (n2 > 0.f) {
+          const float p = 1.f / srun;
+          a.prob[row] = p;
+          a.label[row] = p >= a.tp ? best : -1;
+        } else {
+          a.prob[row] = 0.f;
+          a.label[row] = -1;
+        }
+      }
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(a.tmem_cols)
+                 : "memory");
+  }
+}
+
+// 1 / |q| per query (bf16 rows of length L).
+__global__ void k_query_norms(const __nv_bfloat16* __restrict__ q, int Q, int L, float* qinv) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= Q) return;
+  float s = 0.f;
+  for (int k = lane; k < L; k += 32) {
+    const float v = __bfloat162float(q[(size_t)warp * L + k]);
+    s += v * v;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  if (lane == 0) qinv[warp] = s > 0.f ? rsqrtf(s) : 0.f;
+}
+
+// FP32-stored means -> BF16 copy for the tensor cores, with |m|^2 of the
+// rounded row (so the cosine is that of the vector the tensor cores see).
+// One warp per row.
+__global__ void k_rows_to_bf16(const float* __restrict__ in, __nv_bfloat16* out, float* norm2,
+                               uint32_t rows, int L) {
+  const uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  float s = 0.f;
+  for (int e = 4 * lane; e < L; e += 128) {
+    const float4 v = *reinterpret_cast<const float4*>(in + (size_t)row * L + e);
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+    *reinterpret_cast<__nv_bfloat162*>(out + (size_t)row * L + e) = a;
+    *reinterpret_cast<__nv_bfloat162*>(out + (size_t)row * L + e + 2) = b;
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    s += fa.x * fa.x + fa.y * fa.y + fb.x * fb.x + fb.y * fb.y;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  if (lane == 0) norm2[row] = s;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows,
+                      uint32_t box_inner, uint32_t box_rows) {
+  auto fn = get_encode();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {box_inner, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+size_t query_smem_bytes(int N) {
+  return 1024 + (size_t)kQStages * (kQM * 128 + (size_t)N * 128) + (2 * kQStages + 4) * 8 + 16 +
+         256 * 4;
+}
+
+cudaError_t query_setup_attributes() {
+  return cudaFuncSetAttribute(k_query, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)query_smem_bytes(256));
+}
+
+slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float temperature, float tp,
+                      int32_t* label, float* prob, float* scores, uint32_t n_rows,
+                      cudaStream_t st) {
+  if (n_rows == 0) return SLIM_OK;
+  const int L = m->L;
+  const int N = (Q + 15) / 16 * 16;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(2 * N)) cols <<= 1;
+  const void* A = m->mv.mrow;
+  const float* rn2 = m->mv.mnorm2;
+  int tok = prof_begin(m, SLIM_KERNEL_QUERY, st);
+  if (!m->bf16) {
+    k_rows_to_bf16<<<(unsigned)(((uint64_t)n_rows * 32 + 255) / 256), 256, 0, st>>>(
+        static_cast<const float*>(m->mv.mrow), static_cast<__nv_bfloat16*>(m->qscratch.abf),
+        m->qscratch.rnorm2, n_rows, L);
+    A = m->qscratch.abf;
+    rn2 = m->qscratch.rnorm2;
+  }
+  k_query_norms<<<(Q * 32 + 255) / 256, 256, 0, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(q_dev), Q, L, m->qscratch.qinv);
+  CUtensorMap tA, tB;
+  if (!encode_2d(&tA, A, (uint64_t)L, n_rows, kQK, kQM) ||
+      !encode_2d(&tB, q_dev, (uint64_t)L, (uint64_t)Q, kQK, (uint32_t)N))
+    return fail(SLIM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  QueryArgs a;
+  a.n_rows = n_rows;
+  a.L = L;
+  a.Q = Q;
+  a.N = N;
+  a.tmem_cols = cols;
+  a.inv_temp = 1.f / temperature;
+  a.tp = tp;
+  a.qinv = m->qscratch.qinv;
+  a.rnorm2 = rn2;
+  a.label = label;
+  a.prob = prob;
+  a.scores = scores;
+  a.status = m->mv.ctr;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  const uint32_t tiles = (n_rows + kQM - 1) / kQM;
+  const unsigned grid = (unsigned)std::min<uint32_t>(tiles, (uint32_t)sms);
+  k_query<<<grid, kQThreads, query_smem_bytes(N), st>>>(tA, tB, a);
+  prof_end(m, tok, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  return SLIM_OK;
+}
+
+}  // namespace slim

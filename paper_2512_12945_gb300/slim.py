@@ -21,6 +21,7 @@ from . import build as _build
 SLIM_CLOSED_ONEHOT, SLIM_CLOSED_SOFT, SLIM_OPEN = 0, 1, 2
 SLIM_STORE_F32, SLIM_STORE_BF16 = 0, 1
 SLIM_EXTRACT_POSTERIOR = 1
+AGGREGATION = {"auto": 0, "sort": 1, "hash": 2}
 MODES = {"onehot": SLIM_CLOSED_ONEHOT, "soft": SLIM_CLOSED_SOFT, "open": SLIM_OPEN}
 STATUS = {0: "SLIM_OK", 1: "SLIM_ERR_ARG", 2: "SLIM_ERR_CUDA", 3: "SLIM_ERR_CAPACITY",
           4: "SLIM_ERR_TIMEOUT", 5: "SLIM_ERR_NOMEM", 6: "SLIM_ERR_UNSUPPORTED",
@@ -40,7 +41,8 @@ class slim_map_params(ctypes.Structure):
                 ("embed_dim", ctypes.c_int32), ("embed_storage", ctypes.c_int32),
                 ("alpha0", ctypes.c_double), ("body_from_sensor", ctypes.c_double * 16),
                 ("block_capacity", ctypes.c_int64), ("hash_capacity", ctypes.c_int64),
-                ("voxel_capacity", ctypes.c_int64), ("max_points", ctypes.c_int64)]
+                ("voxel_capacity", ctypes.c_int64), ("max_points", ctypes.c_int64),
+                ("aggregation", ctypes.c_int32), ("tile_points", ctypes.c_int32)]
 
 
 class slim_stats(ctypes.Structure):
@@ -57,7 +59,8 @@ class slim_batch_item(ctypes.Structure):
 EXPORTS = ["slim_map_params_default", "slim_map_create", "slim_map_destroy", "slim_map_reset",
            "slim_integrate", "slim_integrate_host", "slim_map_sync", "slim_map_stats",
            "slim_extract_tsdf", "slim_query", "slim_backward", "slim_integrate_batch",
-           "slim_last_error"]
+           "slim_profile_enable", "slim_profile_read", "slim_autotune", "slim_last_error"]
+KERNELS = ["traverse", "fuse_closed", "open_pairs", "open_apply", "query", "backward", "batch"]
 
 _lock = threading.Lock()
 _lib = None
@@ -92,6 +95,9 @@ def lib():
             "slim_query": [P, P, I32, F, F, P, P, P, P],
             "slim_backward": [P, P, I64, P, P, P, P, P, P, P, P],
             "slim_integrate_batch": [ctypes.POINTER(slim_batch_item), I32, P],
+            "slim_profile_enable": [P, I32],
+            "slim_profile_read": [P, P, P],
+            "slim_autotune": [P, P, I64, P, P, P, ctypes.POINTER(I32)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -242,6 +248,28 @@ def slim_backward(h, pts, pose, sem, gD, gS, gB, width, stream=None):
     return gsem, gxyz
 
 
+def slim_profile_enable(h, on):
+    _check(lib().slim_profile_enable(h, int(bool(on))), "slim_profile_enable")
+
+
+def slim_profile_read(h):
+    """{kernel name: (launches, total ms)} since the last read."""
+    n = (ctypes.c_int64 * 8)()
+    ms = (ctypes.c_double * 8)()
+    _check(lib().slim_profile_read(h, n, ms), "slim_profile_read")
+    return {KERNELS[k]: (int(n[k]), float(ms[k])) for k in range(len(KERNELS)) if n[k]}
+
+
+def slim_autotune(h, pts, pose, sem, width, stream=None):
+    n = pts.shape[0]
+    keep, p_pose = _pose_arr(pose)
+    best = ctypes.c_int32(0)
+    _check(lib().slim_autotune(h, _dev_ptr(pts, torch.float32, "pts", (n, 3)), n, p_pose,
+                               _dev_ptr(sem, torch.float32, "sem", (n, width)), _stream(stream),
+                               ctypes.byref(best)), "slim_autotune")
+    return best.value
+
+
 def slim_integrate_batch(items, stream=None):
     """items: list of (Map, pts, pose, sem)."""
     arr = (slim_batch_item * max(len(items), 1))()
@@ -263,7 +291,8 @@ class Map:
     def __init__(self, voxel_size=0.1, trunc=0.3, mode="onehot", num_classes=20, embed_dim=512,
                  embed_storage="f32", min_range=0.0, max_range=1e30, alpha0=1.0,
                  body_from_sensor=None, block_capacity=100000, hash_capacity=262144,
-                 voxel_capacity=1000000, max_points=1 << 18):
+                 voxel_capacity=1000000, max_points=1 << 18, aggregation="auto",
+                 tile_points=0):
         p = slim_map_params_default()
         p.voxel_size = voxel_size
         p.trunc = trunc
@@ -282,6 +311,8 @@ class Map:
         p.hash_capacity = hash_capacity
         p.voxel_capacity = voxel_capacity
         p.max_points = max_points
+        p.aggregation = AGGREGATION[aggregation] if isinstance(aggregation, str) else aggregation
+        p.tile_points = tile_points
         self.params = p
         self.mode = p.mode
         self.width = embed_dim if p.mode == SLIM_OPEN else num_classes
@@ -319,6 +350,9 @@ class Map:
     def query(self, q_bf16, temperature=0.01, tp=0.1, scores=False, stream=None):
         rows = self.stats(stream)["voxels"]
         return slim_query(self.handle, q_bf16, temperature, tp, rows, scores, stream)
+
+    def autotune(self, pts, pose, sem, stream=None):
+        return slim_autotune(self.handle, pts, pose, sem, self.width, stream)
 
     def backward(self, pts, pose, sem, gD, gS, gB=None, stream=None):
         return slim_backward(self.handle, pts, pose, sem, gD, gS, gB, self.width, stream)

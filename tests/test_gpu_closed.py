@@ -18,9 +18,10 @@ def _built():
     build.build()
 
 
-def test_room_lidar_onehot():
+@pytest.mark.parametrize("agg", ["sort", "hash"])
+def test_room_lidar_onehot(agg):
     w = synth.room_lidar(n_scans=10)
-    g = to_np(gpu_map(w).extract())
+    g = to_np(gpu_map(w, aggregation=agg).extract())
     o = oracle_map(w).extract()
     compare_closed(g, o, "onehot")
     assert np.array_equal(g["sem"].sum(1), g["W"])
@@ -37,9 +38,10 @@ def test_room_posterior_and_alpha0():
         assert_close(g["sem"].sum(1), np.ones(len(g["W"])), 1e-5, 1e-6, "posterior sum")
 
 
-def test_street_lidar_reduced():
+@pytest.mark.parametrize("agg,tile", [("sort", 0), ("hash", 64), ("hash", 128), ("hash", 256)])
+def test_street_lidar_reduced(agg, tile):
     w = synth.street_lidar(n_scans=4, n_beams=64, n_az=512)
-    g = to_np(gpu_map(w).extract())
+    g = to_np(gpu_map(w, aggregation=agg, tile_points=tile).extract())
     o = oracle_map(w).extract()
     compare_closed(g, o, "onehot")
 
@@ -51,7 +53,8 @@ def test_soft_counts():
     compare_closed(g, o, "soft")
 
 
-def test_ragged_empty_and_invalid():
+@pytest.mark.parametrize("agg", ["sort", "hash"])
+def test_ragged_empty_and_invalid(agg):
     """n = 0, single points, a ragged tail, NaN / out-of-range points."""
     w = synth.room_lidar(n_scans=2, n_beams=16, n_az=64)
     s0 = w.scans[0]
@@ -64,7 +67,7 @@ def test_ragged_empty_and_invalid():
              dict(pts=pts[:777], pose=s0["pose"], sem=s0["sem"][:777]),
              w.scans[1]]
     w.scans = scans
-    g = to_np(gpu_map(w).extract())
+    g = to_np(gpu_map(w, aggregation=agg).extract())
     o = oracle_map(w).extract()
     compare_closed(g, o, "onehot")
 
@@ -78,12 +81,13 @@ def test_empty_map_extract():
     assert ext["W"].shape[0] == 0
 
 
-def test_block_capacity_fault_is_reported():
+@pytest.mark.parametrize("agg", ["sort", "hash"])
+def test_block_capacity_fault_is_reported(agg):
     """Too few blocks: the sticky status reports SLIM_ERR_CAPACITY; nothing hangs."""
     from paper_2512_12945_gb300 import slim
     w = synth.room_lidar(n_scans=1)
     m = slim.Map(voxel_size=0.1, trunc=0.3, num_classes=10, min_range=0.1, max_range=100.0,
-                 block_capacity=16, max_points=w.scans[0]["pts"].shape[0])
+                 block_capacity=16, max_points=w.scans[0]["pts"].shape[0], aggregation=agg)
     s = w.scans[0]
     m.integrate(torch.from_numpy(s["pts"]).cuda(), s["pose"], torch.from_numpy(s["sem"]).cuda())
     with pytest.raises(slim.SlimError) as e:
@@ -109,12 +113,25 @@ def test_host_entry_point_matches_device():
     assert_close(ga["D"], gb["D"], RTOL, ATOL, "D")
 
 
-def test_full_size_street_scans_parity():
+@pytest.mark.parametrize("agg", ["sort", "hash"])
+def test_full_size_street_scans_parity(agg):
     """Full launch configuration: 64 x 2048 scans (131,072 points per call)."""
     w = synth.street_lidar(n_scans=2)
-    g = to_np(gpu_map(w).extract())
+    g = to_np(gpu_map(w, aggregation=agg).extract())
     o = oracle_map(w).extract()
     compare_closed(g, o, "onehot")
+
+
+def test_wide_band_and_hash_collisions():
+    """tau = 4 voxels (the widest band: 30-step cap, 128-point tiles) and a
+    tiny hash table (long probe runs) still match the oracle."""
+    w = synth.room_lidar(n_scans=3, n_beams=16, n_az=256)
+    w.trunc = 0.4
+    for agg, tile in (("sort", 0), ("hash", 64), ("hash", 256)):
+        g = to_np(gpu_map(w, aggregation=agg, tile_points=tile, hash_capacity=4096,
+                          block_capacity=3000).extract())
+        o = oracle_map(w).extract()
+        compare_closed(g, o, "onehot")
 
 
 def test_full_size_100_scans_invariants():
@@ -131,3 +148,18 @@ def test_full_size_100_scans_invariants():
         total += len(oracle.scan_pairs(p, s["pts"], s["pose"])[2])
     sub = gpu_map(w, scans=w.scans[::10], block_capacity=400000, hash_capacity=1 << 21)
     assert float(to_np(sub.extract())["W"].sum()) == total
+
+
+def test_autotune_picks_a_tile_and_resets():
+    from paper_2512_12945_gb300 import slim
+    w = synth.street_lidar(n_scans=2)
+    s = w.scans[0]
+    m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=20, min_range=w.min_range,
+                 max_range=w.max_range, body_from_sensor=w.body_from_sensor, max_points=131072)
+    pts, sem = torch.from_numpy(s["pts"]).cuda(), torch.from_numpy(s["sem"]).cuda()
+    best = m.autotune(pts, s["pose"], sem)
+    assert best in (64, 128, 256)
+    assert m.stats()["blocks"] == 0
+    for sc in w.scans:
+        m.integrate(torch.from_numpy(sc["pts"]).cuda(), sc["pose"], torch.from_numpy(sc["sem"]).cuda())
+    compare_closed(to_np(m.extract()), oracle_map(w).extract(), "onehot")
