@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) k_backward(MapView mv, ScanGeom g,
         Wv = mv.tsdf[row].y;
         gi = (size_t)row;
       } else {
-        Wv = mv.rec[vox * mv.rs + 1];
+        Wv = rec_weight(mv.rec + vox * mv.rs, mv.K, mv.split);
         gi = vox;
       }
       const float invW = 1.0f / Wv;

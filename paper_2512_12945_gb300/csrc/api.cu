@@ -187,7 +187,8 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   m->K = p->mode == SLIM_OPEN ? 0 : p->num_classes;
   m->L = p->mode == SLIM_OPEN ? p->embed_dim : 0;
   m->bf16 = (p->mode == SLIM_OPEN && p->embed_storage == SLIM_STORE_BF16) ? 1 : 0;
-  m->rs = ((2 + m->K) + 3) / 4 * 4;
+  // one-hot records keep (S_k, c_k) per class, soft records (S, W, c_k)
+  m->rs = p->mode == SLIM_CLOSED_ONEHOT ? (2 * m->K + 3) / 4 * 4 : ((2 + m->K) + 3) / 4 * 4;
   const double q = 2.0 * (double)p->trunc / (double)p->voxel_size;
   m->cap = 3 * (int)std::ceil(q) + 3;
   const int span = (int)std::ceil(q) + 2;
@@ -217,6 +218,8 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   mv.max_probe = (int32_t)std::min<uint64_t>(m->n_entries, 512);
   mv.block_cap = (uint32_t)bc;
   mv.rs = m->rs;
+  mv.K = m->K;
+  mv.split = p->mode == SLIM_CLOSED_ONEHOT ? 1 : 0;
   if (m->mode != SLIM_OPEN) {
     if ((s = m->alloc(&mv.rec, bc * kBlockVoxels * (uint64_t)m->rs)) != SLIM_OK) return bail(s);
   } else {
@@ -517,9 +520,71 @@ slim_status slim_backward(slim_map* m, const float* pts_dev, int64_t n,
                       (cudaStream_t)stream);
 }
 
-slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, void*) {
-  if (!items && n_items) return fail(SLIM_ERR_ARG, "items is NULL");
-  return fail(SLIM_ERR_UNSUPPORTED, "batched integration not built yet");
+slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, void* stream) {
+  if (n_items < 0) return fail(SLIM_ERR_ARG, "n_items must be >= 0");
+  if (n_items > 0 && !items) return fail(SLIM_ERR_ARG, "items is NULL");
+  for (int32_t k = 0; k < n_items; ++k) {
+    const slim_batch_item& it = items[k];
+    const slim_map* m = it.map;
+    if (!m) return fail(SLIM_ERR_ARG, "item " + std::to_string(k) + ": map is NULL");
+    if (it.n < 0 || it.n > m->p.max_points)
+      return fail(SLIM_ERR_ARG, "item " + std::to_string(k) + ": n must be in [0, max_points]");
+    if (!finite_pose(it.pose)) return fail(SLIM_ERR_ARG, "item " + std::to_string(k) + ": pose");
+    if (it.n > 0 && (!it.pts_dev || !it.sem_dev))
+      return fail(SLIM_ERR_ARG, "item " + std::to_string(k) + ": pts/sem NULL with n > 0");
+    if ((reinterpret_cast<uintptr_t>(it.pts_dev) & 3) ||
+        (reinterpret_cast<uintptr_t>(it.sem_dev) & (m->mode == SLIM_OPEN ? 15 : 3)))
+      return fail(SLIM_ERR_ARG, "item " + std::to_string(k) + ": misaligned pts/sem");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // closed one-hot scans with hash aggregation share persistent launches
+  HashBatch b;
+  b.n_jobs = 0;
+  int tile = 0;
+  auto flush = [&]() -> slim_status {
+    if (b.n_jobs == 0) return SLIM_OK;
+    slim_map* m0 = items[0].map;
+    for (int32_t k = 0; k < n_items; ++k)
+      if (items[k].map->mode == SLIM_CLOSED_ONEHOT && items[k].map->p.aggregation != SLIM_AGG_SORT) {
+        m0 = items[k].map;
+        break;
+      }
+    const int tok = prof_begin(m0, SLIM_KERNEL_BATCH, st);
+    cudaError_t e = launch_hash_batch(b, tile, 0, st);
+    prof_end(m0, tok, st);
+    b.n_jobs = 0;
+    return e == cudaSuccess ? SLIM_OK : cuda_fail(e, "launch_hash_batch");
+  };
+  for (int32_t k = 0; k < n_items; ++k) {
+    const slim_batch_item& it = items[k];
+    slim_map* m = it.map;
+    m->scans++;
+    if (it.n == 0) continue;
+    if (m->mode == SLIM_CLOSED_ONEHOT && m->p.aggregation != SLIM_AGG_SORT) {
+      if (b.n_jobs == 0) {
+        b.work = m->mv.ctr + kCtrWork;
+        tile = m->hash_tile;
+      }
+      HashJob& J = b.job[b.n_jobs++];
+      compose_pose(it.pose, m->p.body_from_sensor, J.g, m->p.voxel_size, m->p.trunc,
+                   m->p.min_range, m->p.max_range, m->cap);
+      J.mv = m->mv;
+      J.pts = it.pts_dev;
+      J.sem = static_cast<const float*>(it.sem_dev);
+      J.n = it.n;
+      J.K = m->K;
+      J.band_blocks = m->band_blocks;
+      if (b.n_jobs == kMaxHashJobs) {
+        slim_status s = flush();
+        if (s != SLIM_OK) return s;
+      }
+    } else {
+      m->scans--;  // counted again by slim_integrate
+      slim_status s = slim_integrate(m, it.pts_dev, it.n, it.pose, it.sem_dev, stream);
+      if (s != SLIM_OK) return s;
+    }
+  }
+  return flush();
 }
 
 }  // extern "C"

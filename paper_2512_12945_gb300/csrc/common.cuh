@@ -16,6 +16,7 @@ enum Counter : int {
   kCtrRows = 1,     // open set: allocated voxel rows
   kCtrStatus = 2,   // sticky status (slim_status value of the first fault)
   kCtrAux = 3,      // diagnostic: where the first fault came from
+  kCtrWork = 5,     // persistent kernels: next tile, finished CTAs (2 words)
   kNumCounters = 8
 };
 
@@ -41,9 +42,15 @@ struct MapView {
   uint64_t* blk_key;    // [block_cap] key of each allocated slot
   uint32_t block_cap;
   uint32_t* ctr;        // kNumCounters counters
-  // closed set: AoS records, rs floats each: {S = W*D, W, c[0..K-1], pad}
+  // closed set: AoS records of rs floats per voxel.
+  //   one-hot (split = 1): {S_0, c_0, S_1, c_1, ..., S_{K-1}, c_{K-1}, pad}
+  //     with c_k the count of class k and S_k the sum of the SDF of those
+  //     observations; W = sum c_k and S = W D = sum S_k at read-out.
+  //   soft (split = 0):    {S = W D, W, c_0 .. c_{K-1}, pad}
   float* rec;
   int32_t rs;
+  int32_t K;
+  int32_t split;
   // open set
   int32_t* vox_row;     // [block_cap * 512] voxel row or -1
   float2* tsdf;         // [row_cap] (S = W*D, W)
@@ -93,6 +100,19 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// addr[0] += a, addr[1] += b as one vector reduction (addr 8-byte aligned).
+__device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
+// Weight W of a closed-set voxel record.
+__device__ __forceinline__ float rec_weight(const float* r, int K, int split) {
+  if (!split) return r[1];
+  float w = 0.f;
+  for (int k = 0; k < K; ++k) w += r[2 * k + 1];
+  return w;
+}
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;

@@ -26,7 +26,7 @@ __device__ __forceinline__ bool voxel_present(const MapView& mv, bool open, uint
     return r >= 0 && mv.tsdf[r].y > 0.f;
   }
   *row = -1;
-  return mv.rec[((size_t)slot * kBlockVoxels + l) * mv.rs + 1] > 0.f;
+  return rec_weight(mv.rec + ((size_t)slot * kBlockVoxels + l) * mv.rs, mv.K, mv.split) > 0.f;
 }
 
 __global__ void __launch_bounds__(256) k_extract_count(MapView mv, const uint32_t* __restrict__ slots,
@@ -77,18 +77,30 @@ __global__ void __launch_bounds__(256) k_extract_write(MapView mv, const uint32_
     }
     if (!open) {
       const float* r = mv.rec + ((size_t)slot * kBlockVoxels + l) * mv.rs;
-      const float S = r[0], W = r[1];
+      // one-hot records hold (S_k, c_k) pairs, soft records (S, W, c_k)
+      const float* cnt = mv.split ? r + 1 : r + 2;
+      const int cs = mv.split ? 2 : 1;
+      float S = 0.f, W = 0.f;
+      if (mv.split) {
+        for (int k = 0; k < a.K; ++k) {
+          S += r[2 * k];
+          W += r[2 * k + 1];
+        }
+      } else {
+        S = r[0];
+        W = r[1];
+      }
       if (a.D) a.D[o] = S / W;
       if (a.W) a.W[o] = W;
       if (a.index) a.index[o] = (int32_t)(slot * kBlockVoxels + l);
       if (a.sem) {
         if (a.flags & SLIM_EXTRACT_POSTERIOR) {
           float tsum = 0.f;
-          for (int k = 0; k < a.K; ++k) tsum += r[2 + k];
+          for (int k = 0; k < a.K; ++k) tsum += cnt[k * cs];
           const float den = (float)a.K * a.alpha0 + tsum;
-          for (int k = 0; k < a.K; ++k) a.sem[o * a.K + k] = (a.alpha0 + r[2 + k]) / den;
+          for (int k = 0; k < a.K; ++k) a.sem[o * a.K + k] = (a.alpha0 + cnt[k * cs]) / den;
         } else {
-          for (int k = 0; k < a.K; ++k) a.sem[o * a.K + k] = r[2 + k];
+          for (int k = 0; k < a.K; ++k) a.sem[o * a.K + k] = cnt[k * cs];
         }
       }
     } else {

@@ -11,8 +11,8 @@
 //      the whole CTA, then published; only then does the CTA wait
 //      (time-bounded) for blocks other CTAs are still publishing, so no wait
 //      can be part of a cycle;
-//   3. flush: S += sum d, W += count, c[class] += count per table entry
-//      (red.add; S = W D, see integrate_closed.cu).
+//   3. flush: one vector red.add (S_k += sum d, c_k += count) per table
+//      entry into the voxel's class-split record (see common.cuh).
 // A pair whose table probe runs out is re-generated after the slots are
 // known and sent to HBM on its own.
 #include "block_sort.cuh"
@@ -27,12 +27,13 @@ constexpr uint32_t kVcEmpty = 0xFFFFFFFFu;
 
 template <int TP>
 struct HashTile {
-  static constexpr int kTbl = 8 * TP;    // block table entries (>= 2 x distinct blocks)
-  static constexpr int kVc = 16 * TP;    // (voxel, class) accumulators
+  static constexpr int kTbl = 4 * TP;    // block table entries (>= distinct blocks of a tile)
+  static constexpr int kVc = 8 * TP;     // (voxel, class) accumulators
   static constexpr int kNew = 4 * TP;    // blocks a tile may create
-  static constexpr int kVcBits = kVc == 4096 ? 12 : (kVc == 2048 ? 11 : 10);
-  static constexpr size_t kSmem = (size_t)kTbl * 8 + (size_t)kTbl * 4 + (size_t)kVc * 12 +
-                                  (size_t)kNew * 2 + 16 * 4;
+  static constexpr int kVcBits = kVc == 2048 ? 11 : (kVc == 1024 ? 10 : 9);
+  // tb_key u64 + tb_slot u32 per block entry, vc_key u32 + (sum, count) u64
+  // per accumulator, new-block list, counters
+  static constexpr size_t kSmem = (size_t)kTbl * 12 + (size_t)kVc * 12 + (size_t)kNew * 2 + 16 * 4;
 };
 
 template <int TP>
@@ -80,6 +81,30 @@ __device__ __forceinline__ int vc_insert(uint32_t* tbl, uint32_t key) {
     h = (h + 1) & (N - 1);
   }
   return -1;
+}
+
+// Accumulator word: FP32 sum in the high half, count in the low half; one
+// compare-and-swap adds an observation (exact FP32 addition, no fixed point).
+__device__ __forceinline__ void acc_add(unsigned long long* a, float d) {
+  unsigned long long cur = *(volatile unsigned long long*)a;
+  for (;;) {
+    const float s = __uint_as_float((uint32_t)(cur >> 32));
+    const unsigned long long nxt =
+        ((unsigned long long)__float_as_uint(__fadd_rn(s, d)) << 32) | ((cur & 0xFFFFFFFFull) + 1ull);
+    const unsigned long long prev = atomicCAS(a, cur, nxt);
+    if (prev == cur) return;
+    cur = prev;
+  }
+}
+
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
 // Index of the largest of K probabilities (ties to the lowest index). The
@@ -135,11 +160,10 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
                                                int tile_points, int64_t tile, unsigned char* sm) {
   using H = HashTile<TP>;
   uint64_t* tb_key = reinterpret_cast<uint64_t*>(sm);
-  uint32_t* tb_slot = reinterpret_cast<uint32_t*>(tb_key + H::kTbl);
+  unsigned long long* vc_acc = reinterpret_cast<unsigned long long*>(tb_key + H::kTbl);
+  uint32_t* tb_slot = reinterpret_cast<uint32_t*>(vc_acc + H::kVc);
   uint32_t* vc_key = tb_slot + H::kTbl;
-  uint32_t* vc_cnt = vc_key + H::kVc;
-  float* vc_sum = reinterpret_cast<float*>(vc_cnt + H::kVc);
-  uint16_t* newe = reinterpret_cast<uint16_t*>(vc_sum + H::kVc);
+  uint16_t* newe = reinterpret_cast<uint16_t*>(vc_key + H::kVc);
   uint32_t* misc = reinterpret_cast<uint32_t*>(newe + H::kNew);
 
   const int tid = threadIdx.x;
@@ -162,8 +186,8 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
   for (int e = tid; e < H::kTbl; e += TP) tb_key[e] = kEmptyKey;
   for (int e = tid; e < H::kVc / 4; e += TP) {
     reinterpret_cast<uint4*>(vc_key)[e] = make_uint4(kVcEmpty, kVcEmpty, kVcEmpty, kVcEmpty);
-    reinterpret_cast<uint4*>(vc_cnt)[e] = make_uint4(0u, 0u, 0u, 0u);
-    reinterpret_cast<float4*>(vc_sum)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    reinterpret_cast<ulonglong2*>(vc_acc)[2 * e] = make_ulonglong2(0ull, 0ull);
+    reinterpret_cast<ulonglong2*>(vc_acc)[2 * e + 1] = make_ulonglong2(0ull, 0ull);
   }
   __syncthreads();
   if (misc[0]) return;
@@ -192,8 +216,7 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
         ovf = idx;
         return;
       }
-      atomicAdd(&vc_cnt[e], 1u);
-      atomicAdd(&vc_sum[e], d);
+      acc_add(&vc_acc[e], d);
     });
   }
   __syncthreads();
@@ -244,7 +267,7 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
       const uint32_t ni = slot < mv.block_cap ? atomicAdd(&misc[1], 1u) : 0u;
       if (slot >= mv.block_cap || ni >= (uint32_t)H::kNew) {
         raise_status(mv.ctr, slot >= mv.block_cap ? kDevCapacity : kDevInternal, 1);
-        *(volatile uint32_t*)&mv.hvals[h] = kFailSlot;
+        st_release(&mv.hvals[h], kFailSlot);
         tb_slot[e] = kFailSlot;
       } else {
         mv.blk_key[slot] = key;
@@ -257,26 +280,33 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
     }
   }
   __syncthreads();
+  // zero the blocks this CTA created, then publish them: every thread fences
+  // its own zero stores (a fence orders only the issuing thread's writes)
+  // before the barrier, so the slot is published after all of them
   const uint32_t nnew = min(misc[1], (uint32_t)H::kNew);
-  for (uint32_t i = 0; i < nnew; ++i) {
-    float4* p = reinterpret_cast<float4*>(mv.rec + (size_t)tb_slot[newe[i]] * kBlockVoxels * mv.rs);
-    const int n4 = kBlockVoxels * mv.rs / 4;
-    for (int k = tid; k < n4; k += TP) p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  __threadfence();
-  __syncthreads();
+  if (nnew) {
+    for (uint32_t i = 0; i < nnew; ++i) {
+      float4* p = reinterpret_cast<float4*>(mv.rec + (size_t)tb_slot[newe[i]] * kBlockVoxels * mv.rs);
+      const int n4 = kBlockVoxels * mv.rs / 4;
+      for (int k = tid; k < n4; k += TP) p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __threadfence();
+    __syncthreads();
 #pragma unroll
-  for (int q = 0; q < Q; ++q)
-    if (created & (1u << q)) *(volatile uint32_t*)&mv.hvals[hpos[q]] = tb_slot[tid + q * TP];
+    for (int q = 0; q < Q; ++q)
+      if (created & (1u << q)) st_release(&mv.hvals[hpos[q]], tb_slot[tid + q * TP]);
+  }
+  // resolve the blocks other CTAs created (acquire: their zeroing is visible
+  // before this CTA's reductions, which depend on the slot read here)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int e = tid + q * TP;
     if (tb_key[e] == kEmptyKey || tb_slot[e] != kNoSlot) continue;
-    volatile uint32_t* hv = &mv.hvals[hpos[q]];
-    uint32_t v = *hv;
+    uint32_t* hv = &mv.hvals[hpos[q]];
+    uint32_t v = ld_acquire(hv);
     if (v == kNoSlot) {
       const uint64_t t0 = global_ns();
-      while ((v = *hv) == kNoSlot) {
+      while ((v = ld_acquire(hv)) == kNoSlot) {
         if (global_ns() - t0 > kCrossCtaWaitNs) {
           raise_status(mv.ctr, kDevTimeout, 5);
           v = kFailSlot;
@@ -285,22 +315,31 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
         __nanosleep(100);
       }
     }
+    if (v != kFailSlot && v >= mv.block_cap) {  // consistency check, never expected
+      raise_status(mv.ctr, kDevInternal, 9);
+      v = kFailSlot;
+    }
     tb_slot[e] = v;
   }
-  __threadfence();
   __syncthreads();
 
-  // 3. flush: one red.add each for S, W and the class count per entry
+  // 3. flush: one vector red.add (S_k, c_k) per entry
   for (int e = tid; e < H::kVc; e += TP) {
     const uint32_t key = vc_key[e];
     if (key == kVcEmpty) continue;
+    if ((key >> 15) >= (uint32_t)H::kTbl) {  // consistency check, never expected
+      raise_status(mv.ctr, kDevInternal, 6);
+      continue;
+    }
     const uint32_t slot = tb_slot[key >> 15];
     if (slot >= kFailSlot) continue;
+    if (slot >= mv.block_cap || (key & 63u) >= (uint32_t)mv.K) {
+      raise_status(mv.ctr, kDevInternal, 7);
+      continue;
+    }
     float* r = mv.rec + ((size_t)slot * kBlockVoxels + ((key >> 6) & 511u)) * mv.rs;
-    const float c = (float)vc_cnt[e];
-    atomicAdd(r, vc_sum[e]);
-    atomicAdd(r + 1, c);
-    atomicAdd(r + 2 + (key & 63u), c);
+    const unsigned long long a = vc_acc[e];
+    red_add_v2(r + 2 * (key & 63u), __uint_as_float((uint32_t)(a >> 32)), (float)(uint32_t)a);
   }
 
   // 4. pairs the table could not take go to HBM one by one
@@ -316,59 +355,120 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
         slot = te == 0xFFFFFFFFu ? kFailSlot : tb_slot[te];
       }
       if (k++ < ovf || slot >= kFailSlot) return;
+      if (slot >= mv.block_cap) {
+        raise_status(mv.ctr, kDevInternal, 8);
+        return;
+      }
       float* r = mv.rec + ((size_t)slot * kBlockVoxels + local_index(i0, i1, i2)) * mv.rs;
-      atomicAdd(r, d);
-      atomicAdd(r + 1, 1.f);
-      atomicAdd(r + 2 + cls, 1.f);
+      red_add_v2(r + 2 * cls, d, 1.f);
     });
   }
 }
 
+// Persistent form: a grid sized to the resident capacity takes tiles from a
+// shared counter until every tile of every job (a scan of some map) is done;
+// the last CTA to finish resets the counter for the next launch. Tiles of
+// different jobs (scans of the same or of different maps) run concurrently:
+// the per-scan updates are additions (Theorem 1), so their order is free.
 template <int TP>
-__global__ void __launch_bounds__(TP) k_fuse_hash(MapView mv, ScanGeom g,
-                                                  const float* __restrict__ pts,
-                                                  const float* __restrict__ sem, int64_t n, int K,
-                                                  int tile_points) {
+__global__ void __launch_bounds__(TP, 1024 / TP) k_fuse_hash_persistent(const __grid_constant__ HashBatch b) {
   extern __shared__ __align__(16) unsigned char sm[];
-  fuse_hash_tile<TP>(mv, g, pts, sem, n, K, tile_points, blockIdx.x, sm);
+  __shared__ uint32_t s_t;
+  for (;;) {
+    if (threadIdx.x == 0) s_t = atomicAdd(&b.work[0], 1u);
+    __syncthreads();
+    const uint32_t t = s_t;
+    __syncthreads();
+    if (t >= b.total_tiles) break;
+    int jb = 0;
+    while (jb + 1 < b.n_jobs && t >= b.job[jb + 1].tile_begin) ++jb;
+    const HashJob& J = b.job[jb];
+    fuse_hash_tile<TP>(J.mv, J.g, J.pts, J.sem, J.n, J.K, J.tile_points, (int64_t)(t - J.tile_begin),
+                       sm);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&b.work[1], 1u) == gridDim.x - 1) {
+      b.work[0] = 0;
+      b.work[1] = 0;
+    }
+  }
+}
+
+static int g_resident[3] = {0, 0, 0};  // CTAs per SM of the 64 / 128 / 256 variants
+static int g_sms = 0;
+
+template <int TP>
+static cudaError_t setup_one(int idx) {
+  cudaError_t e = cudaFuncSetAttribute(k_fuse_hash_persistent<TP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)HashTile<TP>::kSmem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_resident[idx], k_fuse_hash_persistent<TP>,
+                                                       TP, HashTile<TP>::kSmem);
 }
 
 cudaError_t hash_setup_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_fuse_hash<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)HashTile<64>::kSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fuse_hash<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)HashTile<128>::kSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fuse_hash<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)HashTile<256>::kSmem);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = setup_one<64>(0);
+  if (e == cudaSuccess) e = setup_one<128>(1);
+  if (e == cudaSuccess) e = setup_one<256>(2);
   return e;
 }
 
 // Largest number of points a TP-thread tile may hold: its distinct blocks
-// (at most points x band_blocks) must fit the block table at half load.
+// (at most points x band_blocks) must fit the block table.
 int hash_tile_points(int TP, int band_blocks) {
   int tp = TP;
-  while (tp > 16 && tp * band_blocks > 4 * TP) tp >>= 1;
+  while (tp > 16 && tp * band_blocks > HashTile<256>::kTbl / 256 * TP) tp >>= 1;
   return tp;
 }
 
 int hash_max_tile(int band_blocks) { return hash_tile_points(256, band_blocks); }
 
+// Fill the tile ranges of b's jobs and launch the persistent kernel.
+// `tile` selects the variant (64, 128 or 256 threads); ctas_per_sm = 0 uses
+// the resident maximum.
+cudaError_t launch_hash_batch(HashBatch& b, int tile, int ctas_per_sm, cudaStream_t st) {
+  const int TP = tile <= 64 ? 64 : (tile <= 128 ? 128 : 256);
+  const int idx = TP == 64 ? 0 : (TP == 128 ? 1 : 2);
+  uint32_t total = 0;
+  for (int j = 0; j < b.n_jobs; ++j) {
+    b.job[j].tile_points = hash_tile_points(TP, b.job[j].band_blocks);
+    b.job[j].tile_begin = total;
+    total += (uint32_t)((b.job[j].n + b.job[j].tile_points - 1) / b.job[j].tile_points);
+  }
+  b.total_tiles = total;
+  if (total == 0) return cudaSuccess;
+  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, g_resident[idx]) : g_resident[idx];
+  const uint32_t grid = std::min<uint32_t>(total, (uint32_t)std::max(1, per_sm * g_sms));
+  if (TP == 64)
+    k_fuse_hash_persistent<64><<<grid, 64, HashTile<64>::kSmem, st>>>(b);
+  else if (TP == 128)
+    k_fuse_hash_persistent<128><<<grid, 128, HashTile<128>::kSmem, st>>>(b);
+  else
+    k_fuse_hash_persistent<256><<<grid, 256, HashTile<256>::kSmem, st>>>(b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fuse_hash(const MapView& mv, const ScanGeom& g, const float* pts,
                              const float* sem, int64_t n, int K, int tile, int band_blocks,
                              cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const int TP = tile <= 64 ? 64 : (tile <= 128 ? 128 : 256);
-  const int tp = hash_tile_points(TP, band_blocks);
-  const unsigned grid = (unsigned)((n + tp - 1) / tp);
-  if (TP == 64)
-    k_fuse_hash<64><<<grid, 64, HashTile<64>::kSmem, st>>>(mv, g, pts, sem, n, K, tp);
-  else if (TP == 128)
-    k_fuse_hash<128><<<grid, 128, HashTile<128>::kSmem, st>>>(mv, g, pts, sem, n, K, tp);
-  else
-    k_fuse_hash<256><<<grid, 256, HashTile<256>::kSmem, st>>>(mv, g, pts, sem, n, K, tp);
-  return cudaGetLastError();
+  HashBatch b;
+  b.n_jobs = 1;
+  b.job[0].mv = mv;
+  b.job[0].g = g;
+  b.job[0].pts = pts;
+  b.job[0].sem = sem;
+  b.job[0].n = n;
+  b.job[0].K = K;
+  b.job[0].band_blocks = band_blocks;
+  b.work = mv.ctr + kCtrWork;
+  return launch_hash_batch(b, tile, 0, st);
 }
 
 }  // namespace slim

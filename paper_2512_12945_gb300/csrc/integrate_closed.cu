@@ -15,12 +15,13 @@
 // k_traverse_alloc (the block-allocation pass on its own) serves the
 // open-set path, whose pair pass needs every slot published beforehand.
 //
-// Voxel record (AoS, rs floats, 16-byte aligned): {S, W, c_0 .. c_{K-1}, pad}
-// with S = W * D. With w~ = 1 the paper's running average
+// Voxel records (AoS, rs floats, 16-byte aligned; layouts in common.cuh)
+// keep sums: S = W * D instead of D. With w~ = 1 the paper's running average
 // D_t = (W_{t-1} D_{t-1} + d_t) / W_t is the same as S_t = S_{t-1} + d_t,
 // W_t = W_{t-1} + 1 and D = S / W at read-out; keeping S makes every update
 // of a scan an addition, so partial sums from different tiles merge exactly
-// in any order (Theorem 1 for the counts).
+// in any order (Theorem 1 for the counts). One-hot records split S and W by
+// class, so one vector reduction carries a (voxel, class) partial.
 #include "block_sort.cuh"
 #include "common.cuh"
 #include "geometry.cuh"
@@ -328,7 +329,9 @@ __global__ void __launch_bounds__(256, 2)
   const uint32_t* sorted = cta_radix_sort(sA, sB, (int)npairs, 13, 9 + tbits, hist, wtot);
 
   // 5. warp segmented reduction over 32-pair windows of the sorted pairs;
-  //    the first lane of each voxel run flushes its sums.
+  //    the first lane of each run flushes its sums. hist is free again and
+  //    gives each warp 32 floats of scratch.
+  float* ws = reinterpret_cast<float*>(hist) + warp * 32;
   for (int wb = (int)warp * 32; wb < (int)npairs; wb += kCtaThreads) {
     const int i = wb + (int)lane;
     const bool act = i < (int)npairs;
@@ -336,32 +339,36 @@ __global__ void __launch_bounds__(256, 2)
     const uint32_t key2 = act ? (c >> 13) : 0xFFFFFFFFu;
     const uint32_t raw = c & 0x1FFFu;
     const int pt = act ? (int)(raw & (uint32_t)(tile_points - 1)) : 0;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key2);
-    const int first = __ffs(peers) - 1, lastl = 31 - __clz(peers);
-    float dsum = act ? pd[raw] : 0.f;
-    float cnt = act ? 1.f : 0.f;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const float a1 = __shfl_down_sync(0xFFFFFFFFu, dsum, off);
-      const float a2 = __shfl_down_sync(0xFFFFFFFFu, cnt, off);
-      if ((int)lane + off <= lastl) {
-        dsum += a1;
-        cnt += a2;
-      }
-    }
     const uint32_t slot = act ? tb_slot[key2 >> 9] : kNoSlot;
     float* r = (slot < kFailSlot) ? mv.rec + ((size_t)slot * kBlockVoxels + (key2 & 511u)) * mv.rs
-                                 : nullptr;
-    if (r && (int)lane == first) {
-      atomicAdd(r, dsum);
-      atomicAdd(r + 1, cnt);
-    }
+                                  : nullptr;
     if (MODE == 0) {
+      // (voxel, class) groups: sum d per group leader through warp scratch
       const uint32_t cl = cls[pt];
       const uint32_t kc = act ? ((key2 << 7) | cl) : 0xFFFFFFFFu;
       const unsigned pc = __match_any_sync(0xFFFFFFFFu, kc);
-      if (r && (int)lane == __ffs(pc) - 1) atomicAdd(r + 2 + cl, (float)__popc(pc));
+      const int ldr = __ffs(pc) - 1;
+      ws[lane] = 0.f;
+      __syncwarp();
+      if (act) atomicAdd(&ws[ldr], pd[raw]);
+      __syncwarp();
+      if (r && (int)lane == ldr) red_add_v2(r + 2 * cl, ws[lane], (float)__popc(pc));
+      __syncwarp();
     } else {
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, key2);
+      const int first = __ffs(peers) - 1, lastl = 31 - __clz(peers);
+      float dsum = act ? pd[raw] : 0.f;
+      float cnt = act ? 1.f : 0.f;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float a1 = __shfl_down_sync(0xFFFFFFFFu, dsum, off);
+        const float a2 = __shfl_down_sync(0xFFFFFFFFu, cnt, off);
+        if ((int)lane + off <= lastl) {
+          dsum += a1;
+          cnt += a2;
+        }
+      }
+      if (r && (int)lane == first) red_add_v2(r, dsum, cnt);
       for (int k = 0; k < K; ++k) {
         float pv = act ? probs[pt * K + k] : 0.f;
 #pragma unroll

@@ -17,6 +17,25 @@ cudaError_t launch_fuse_closed(const MapView& mv, const ScanGeom& g, const float
                                cudaStream_t st);
 cudaError_t closed_setup_attributes(int mode, int K, int tile_points);
 // fuse_hash.cu: one-hot hash aggregation; tile = points per CTA (64, 128 or 256)
+struct HashJob {
+  MapView mv;
+  ScanGeom g;
+  const float* pts;
+  const float* sem;
+  int64_t n;
+  int32_t K;
+  int32_t band_blocks;
+  int32_t tile_points;  // set by launch_hash_batch
+  uint32_t tile_begin;  // set by launch_hash_batch
+};
+constexpr int kMaxHashJobs = 16;
+struct HashBatch {
+  HashJob job[kMaxHashJobs];
+  int32_t n_jobs;
+  uint32_t total_tiles;
+  uint32_t* work;  // two zeroed device words (next tile, finished CTAs)
+};
+cudaError_t launch_hash_batch(HashBatch& b, int tile, int ctas_per_sm, cudaStream_t st);
 cudaError_t hash_setup_attributes();
 cudaError_t launch_fuse_hash(const MapView& mv, const ScanGeom& g, const float* pts,
                              const float* sem, int64_t n, int K, int tile, int band_blocks,
