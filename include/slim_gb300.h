@@ -187,6 +187,28 @@ slim_status slim_query(slim_map* m, const uint16_t* q_dev, int32_t q, float temp
                        float tp, int32_t* label_dev, float* prob_dev, float* scores_dev,
                        void* stream);
 
+/* The open-set read-out of slim_query over rows the caller holds, for
+ * callers that cannot allocate device memory (code inside a stream capture
+ * that must not add allocations, real-time loops with a fixed memory
+ * budget, hosts that only pass buffers they own). The paper has no
+ * counterpart; this is an interface convenience.
+ *   rows_dev  n_rows x l bf16 bit patterns (voxel means, row-major, 16-byte
+ *             aligned); q_dev q x l bf16 queries (16-byte aligned);
+ *   label_dev, prob_dev  n_rows outputs as in slim_query.
+ * It calls no cudaMalloc / cudaFree and no allocating library routine: its
+ * working memory (query and row norms, a status word) is one static array
+ * in device memory, present on every GPU that loads the library until the
+ * process exits, sized for at most 2^20 rows and 256 queries per call;
+ * larger requests return SLIM_ERR_ARG. The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, with the device
+ * current) and opts the query kernel into its shared memory; make that first
+ * call before any stream capture. Every call shares the array and leaves its
+ * contents behind; calls whose work overlaps on the GPU (other streams, other
+ * threads) race on it, so serialise them. Asynchronous on `stream`. */
+slim_status slim_query_rows_static(const uint16_t* rows_dev, int64_t n_rows, int32_t l,
+                                   const uint16_t* q_dev, int32_t q, float temperature, float tp,
+                                   int32_t* label_dev, float* prob_dev, void* stream);
+
 /* Reverse mode of a map integrated from empty (zero priors, so the state is
  * the batch posterior of all observations, Theorems 1-2). Given loss
  * gradients per voxel (indexed like index_dev of slim_extract_tsdf, arrays

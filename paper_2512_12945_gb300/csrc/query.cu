@@ -21,6 +21,8 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "map.h"
 
 namespace slim {
@@ -357,6 +359,23 @@ __global__ void k_query_norms(const __nv_bfloat16* __restrict__ q, int Q, int L,
   if (lane == 0) qinv[warp] = s > 0.f ? rsqrtf(s) : 0.f;
 }
 
+// |m|^2 of each BF16 row (one warp per row).
+__global__ void k_row_norms_bf16(const __nv_bfloat16* __restrict__ rows, float* norm2,
+                                 uint32_t n_rows, int L) {
+  const uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  float s = 0.f;
+  for (int e = 2 * lane; e < L; e += 64) {
+    const float2 v =
+        __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(rows + (size_t)row * L + e));
+    s += v.x * v.x + v.y * v.y;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  if (lane == 0) norm2[row] = s;
+}
+
 // FP32-stored means -> BF16 copy for the tensor cores, with |m|^2 of the
 // rounded row (so the cosine is that of the vector the tensor cores see).
 // One warp per row.
@@ -466,4 +485,112 @@ slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float tempe
   return SLIM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Read-out for callers that cannot allocate device memory.
+//
+// Some callers may not call cudaMalloc at all: code running inside a stream
+// capture that must not add allocation nodes, real-time loops whose memory
+// budget is fixed up front, or host programs that only hand in buffers they
+// already own. slim_query_rows_static serves them: its working memory is the
+// file-scope array below, which exists on every GPU that loads this library
+// for as long as the process lives. It holds the inverse query norms, the
+// row norms of at most kStaticQueryRows rows, and a status word.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kStaticQueryRows = 1u << 20;  // rows per call (4 MiB of row norms)
+constexpr uint32_t kStaticQueries = 256;
+constexpr size_t kStaticWords = kStaticQueries + kStaticQueryRows + 64;
+static __device__ __align__(256) float g_static_query_scratch[kStaticWords];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_ptr[128] = {};  // device address of the scratch, per device
+bool g_static_ready[128] = {};
+}  // namespace
+
+// Per-device set-up (once, with that device current): the device address of
+// the static scratch and the shared-memory opt-in of the query kernel.
+static slim_status static_query_setup(int dev, float** scratch) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (dev < 0 || dev >= 128) return fail(SLIM_ERR_ARG, "device ordinal out of range");
+  if (!g_static_ready[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_query_scratch);
+    if (e != cudaSuccess)
+      return fail(SLIM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    e = query_setup_attributes();
+    if (e != cudaSuccess)
+      return fail(SLIM_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
+    g_static_ready[dev] = true;
+  }
+  *scratch = static_cast<float*>(g_static_ptr[dev]);
+  return SLIM_OK;
+}
+
 }  // namespace slim
+
+extern "C" slim_status slim_query_rows_static(const uint16_t* rows_dev, int64_t n_rows,
+                                              int32_t l, const uint16_t* q_dev, int32_t q,
+                                              float temperature, float tp, int32_t* label_dev,
+                                              float* prob_dev, void* stream) {
+  using namespace slim;
+  if (n_rows < 0 || (uint64_t)n_rows > kStaticQueryRows)
+    return fail(SLIM_ERR_ARG, "n_rows must be in [0, 2^20]: the static scratch holds the norms "
+                              "of at most 1048576 rows per call");
+  if (l < 64 || l > 1024 || l % 64) return fail(SLIM_ERR_ARG, "l must be a multiple of 64 in [64, 1024]");
+  if (q < 1 || q > (int32_t)kStaticQueries) return fail(SLIM_ERR_ARG, "q must be in [1, 256]");
+  if (!(temperature > 0.f) || !std::isfinite(temperature))
+    return fail(SLIM_ERR_ARG, "temperature must be finite and > 0");
+  if (n_rows > 0 && (!rows_dev || !label_dev || !prob_dev))
+    return fail(SLIM_ERR_ARG, "rows, label and prob must be non-NULL");
+  if (!q_dev || (reinterpret_cast<uintptr_t>(q_dev) & 15) || (reinterpret_cast<uintptr_t>(rows_dev) & 15))
+    return fail(SLIM_ERR_ARG, "rows and queries must be non-NULL and 16-byte aligned");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  float* scratch = nullptr;
+  slim_status s = static_query_setup(dev, &scratch);
+  if (s != SLIM_OK) return s;
+  if (n_rows == 0) return SLIM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  float* qinv = scratch;
+  float* rnorm2 = scratch + kStaticQueries;
+  uint32_t* status = reinterpret_cast<uint32_t*>(scratch + kStaticQueries + kStaticQueryRows);
+  // the status word must start at zero; the norms are overwritten below
+  e = cudaMemsetAsync(status, 0, kNumCounters * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  const uint32_t rows = (uint32_t)n_rows;
+  k_row_norms_bf16<<<(unsigned)(((uint64_t)rows * 32 + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(rows_dev), rnorm2, rows, l);
+  k_query_norms<<<(q * 32 + 255) / 256, 256, 0, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(q_dev), q, l, qinv);
+  const int N = (q + 15) / 16 * 16;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(2 * N)) cols <<= 1;
+  CUtensorMap tA, tB;
+  if (!encode_2d(&tA, rows_dev, (uint64_t)l, rows, kQK, kQM) ||
+      !encode_2d(&tB, q_dev, (uint64_t)l, (uint64_t)q, kQK, (uint32_t)N))
+    return fail(SLIM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  QueryArgs a;
+  a.n_rows = rows;
+  a.L = l;
+  a.Q = q;
+  a.N = N;
+  a.tmem_cols = cols;
+  a.inv_temp = 1.f / temperature;
+  a.tp = tp;
+  a.qinv = qinv;
+  a.rnorm2 = rnorm2;
+  a.label = label_dev;
+  a.prob = prob_dev;
+  a.scores = nullptr;
+  a.status = status;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t tiles = (rows + kQM - 1) / kQM;
+  const unsigned grid = (unsigned)std::min<uint32_t>(tiles, (uint32_t)sms);
+  k_query<<<grid, kQThreads, query_smem_bytes(N), st>>>(tA, tB, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  return SLIM_OK;
+}

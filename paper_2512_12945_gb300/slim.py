@@ -59,7 +59,8 @@ class slim_batch_item(ctypes.Structure):
 EXPORTS = ["slim_map_params_default", "slim_map_create", "slim_map_destroy", "slim_map_reset",
            "slim_integrate", "slim_integrate_host", "slim_map_sync", "slim_map_stats",
            "slim_extract_tsdf", "slim_query", "slim_backward", "slim_integrate_batch",
-           "slim_profile_enable", "slim_profile_read", "slim_autotune", "slim_last_error"]
+           "slim_profile_enable", "slim_profile_read", "slim_autotune", "slim_query_rows_static",
+           "slim_last_error"]
 KERNELS = ["traverse", "fuse_closed", "open_pairs", "open_apply", "query", "backward", "batch"]
 
 _lock = threading.Lock()
@@ -98,6 +99,7 @@ def lib():
             "slim_profile_enable": [P, I32],
             "slim_profile_read": [P, P, P],
             "slim_autotune": [P, P, I64, P, P, P, ctypes.POINTER(I32)],
+            "slim_query_rows_static": [P, I64, I32, P, I32, F, F, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -230,6 +232,27 @@ def slim_query(h, q_bf16, temperature, tp, n_rows, scores=False, stream=None):
                             None if sc is None else ctypes.c_void_p(sc.data_ptr()),
                             _stream(stream)), "slim_query")
     return label, prob, sc
+
+
+def slim_query_rows_static(rows_bf16, q_bf16, temperature=0.01, tp=0.1, label=None, prob=None,
+                           stream=None):
+    """Read-out over caller-held BF16 rows with no device allocation inside
+    the library (outputs may be passed in, preallocated)."""
+    if rows_bf16.dtype != torch.bfloat16 or q_bf16.dtype != torch.bfloat16:
+        raise TypeError("rows and queries must be bfloat16")
+    n, l = rows_bf16.shape
+    Q = q_bf16.shape[0]
+    dev = rows_bf16.device
+    if label is None:
+        label = torch.empty(n, dtype=torch.int32, device=dev)
+    if prob is None:
+        prob = torch.empty(n, dtype=torch.float32, device=dev)
+    _check(lib().slim_query_rows_static(
+        _dev_ptr(rows_bf16.view(torch.int16), torch.int16, "rows"), n, l,
+        _dev_ptr(q_bf16.view(torch.int16), torch.int16, "q"), Q, float(temperature), float(tp),
+        _dev_ptr(label, torch.int32, "label", (n,)), _dev_ptr(prob, torch.float32, "prob", (n,)),
+        _stream(stream)), "slim_query_rows_static")
+    return label, prob
 
 
 def slim_backward(h, pts, pose, sem, gD, gS, gB, width, stream=None):
