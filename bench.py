@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--scans", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="0: same as --steps (max 10)")
+    ap.add_argument("--workload", choices=["street", "room", "indoor", "adjoint", "batch"],
+                    default="street", help="street (default, the headline line) or a "
+                    "secondary configuration, each printing its own JSON line")
+    ap.add_argument("--frames", type=int, default=4, help="indoor: RGB-D frames per step")
+    ap.add_argument("--block-capacity", type=int, default=65536,
+                    help="street: 8^3 blocks reserved per map (100 scans use ~26k)")
     return ap.parse_args()
 
 
@@ -156,8 +162,12 @@ def algorithmic_bytes(counts, n_scans):
 
 
 def kernel_source_sha():
-    p = os.path.join(ROOT, "paper_2512_12945_gb300", "csrc", "integrate_closed.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """Hash of the sources of the dominant kernel (k_fuse_hash_persistent)."""
+    h = hashlib.sha256()
+    for f in ("fuse_hash.cu", "common.cuh", "geometry.cuh", "hash.cuh"):
+        with open(os.path.join(ROOT, "paper_2512_12945_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def stored_traffic():
@@ -243,7 +253,8 @@ def run_ours(args):
     w = synth.street_lidar(n_scans=args.scans)
     m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=w.num_classes,
                  min_range=w.min_range, max_range=w.max_range, body_from_sensor=w.body_from_sensor,
-                 block_capacity=400000, hash_capacity=1 << 21, max_points=131072)
+                 block_capacity=args.block_capacity, hash_capacity=1 << 21,
+                 max_points=131072)
     h = m.handle
     pts = [torch.from_numpy(s["pts"]).cuda() for s in w.scans]
     sem = [torch.from_numpy(s["sem"]).cuda() for s in w.scans]
@@ -418,7 +429,7 @@ def run_ours(args):
     for agg in ("sort",):
         mv = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=w.num_classes,
                       min_range=w.min_range, max_range=w.max_range,
-                      body_from_sensor=w.body_from_sensor, block_capacity=400000,
+                      body_from_sensor=w.body_from_sensor, block_capacity=args.block_capacity,
                       hash_capacity=1 << 21, max_points=131072, aggregation=agg)
         hv = mv.handle
 
@@ -464,10 +475,258 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------- other configs
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def run_indoor(args):
+    """Open-set RGB-D frames (640x480, l = 512), FP32 vs BF16 storage, and the
+    tensor-core query of 256 embeddings against every voxel."""
+    import numpy as np
+    import torch
+    from paper_2512_12945_gb300 import build, slim, synth
+    build.build()
+    torch.cuda.set_device(0)
+    w = synth.indoor_rgbd(seed=3, n_frames=200, width=640, height=480, dim=512,
+                          frames=list(range(args.frames)))
+    pts = [torch.from_numpy(s["pts"]).cuda() for s in w.scans]
+    sem = [torch.from_numpy(s["sem"]).cuda() for s in w.scans]
+    valid = sum(int((np.linalg.norm(s["pts"], axis=1) >= w.min_range).sum()) for s in w.scans)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for storage in ("f32", "bf16"):
+        m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, mode="open", embed_dim=512,
+                     embed_storage=storage, min_range=w.min_range, max_range=w.max_range,
+                     max_points=640 * 480, block_capacity=200000, hash_capacity=1 << 20,
+                     voxel_capacity=2_000_000)
+
+        def step():
+            m.reset()
+            for p, q, s in zip(pts, sem, w.scans):
+                m.integrate(p, s["pose"], q)
+
+        for _ in range(args.warmup):
+            step()
+        slim.slim_profile_enable(m.handle, True)
+        ms = _timed(step, args.steps, 0, stream)
+        prof = slim.slim_profile_read(m.handle)
+        slim.slim_profile_enable(m.handle, False)
+        m.sync()
+        rows = m.stats()["voxels"]
+        q = torch.from_numpy(synth.random_queries(7, 256, 512)).to(torch.bfloat16).cuda()
+        for _ in range(args.warmup):
+            m.query(q, 0.01, 0.1)
+        slim.slim_profile_enable(m.handle, True)
+        qms = _timed(lambda: m.query(q, 0.01, 0.1), args.steps, 0, stream)
+        qprof = slim.slim_profile_read(m.handle)
+        slim.slim_profile_enable(m.handle, False)
+        nq, qkms = qprof.get("query", (1, qms))
+        kq = qkms / max(nq, 1)
+        flops = 2.0 * rows * 512 * 256
+        peak, kind = _bf16_peak()
+        out[storage] = {"points_per_s": valid * args.steps / (ms * args.steps / 1e3),
+                        "ms_per_step": ms, "voxels": rows,
+                        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+                        "query": {"ms": qms, "kernel_ms": kq, "tflops": flops / (kq / 1e3) / 1e12,
+                                  "roofline": {"bound": "tensor", "peak": peak, "unit": "TFLOP/s",
+                                               "frac": flops / (kq / 1e3) / 1e12 / peak,
+                                               "peak_source": kind},
+                                  "hbm_gbs": rows * (2 * 512 + 8) / (kq / 1e3) / 1e9}}
+        m.close()
+    line = {"metric": "open-set points integrated/s (NIG, l=512) and query TFLOP/s",
+            "value": out["bf16"]["points_per_s"], "unit": "points/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f32 accumulate, bf16 storage", "data": "synthetic",
+            "config": {"workload": f"indoor-rgbd {args.frames} frames 640x480, l=512, voxel "
+                                   "0.05 m, trunc 0.15 m, 256 queries T=0.01"},
+            "storage": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_adjoint(args):
+    """Forward integration + reverse mode on the room scene with 64 x 2048
+    scans, soft counts (20 classes)."""
+    import numpy as np
+    import torch
+    from paper_2512_12945_gb300 import autograd, build, slim, synth
+    build.build()
+    torch.cuda.set_device(0)
+    w = synth.room_lidar(seed=4, n_scans=20, n_beams=64, n_az=2048, K=20, mode="soft")
+    m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, mode="soft", num_classes=20,
+                 min_range=w.min_range, max_range=w.max_range, max_points=131072,
+                 block_capacity=100000, hash_capacity=1 << 20)
+    pts = [torch.from_numpy(s["pts"]).cuda().requires_grad_(True) for s in w.scans]
+    sem = [torch.from_numpy(s["sem"]).cuda().requires_grad_(True) for s in w.scans]
+    poses = [s["pose"] for s in w.scans]
+    rng = np.random.default_rng(4)
+    stream = torch.cuda.current_stream()
+    state = {}
+
+    def fwd():
+        D, W, c, ijk = autograd.integrate(m, poses, pts, sem)
+        state["out"] = (D, c)
+
+    def fwd_bwd():
+        D, W, c, ijk = autograd.integrate(m, poses, pts, sem)
+        n = D.shape[0]
+        if "sel" not in state or state["n"] != n:
+            state["n"] = n
+            state["sel"] = torch.from_numpy(rng.choice(n, min(10000, n), replace=False)).cuda()
+            state["y"] = torch.from_numpy(rng.integers(0, 20, min(10000, n))).cuda()
+        sel, y = state["sel"], state["y"]
+        post = (1.0 + c[sel]) / (20.0 + c[sel].sum(1, keepdim=True))
+        loss = (D[sel] ** 2).sum() + torch.nn.functional.nll_loss(torch.log(post), y, reduction="sum")
+        for t in pts + sem:
+            t.grad = None
+        loss.backward()
+
+    fms = _timed(fwd, args.steps, args.warmup, stream)
+    torch.cuda.reset_peak_memory_stats()
+    base = torch.cuda.memory_allocated()
+    tms = _timed(fwd_bwd, args.steps, args.warmup, stream)
+    peak = torch.cuda.max_memory_allocated() - base
+    valid = sum(int((np.linalg.norm(s["pts"], axis=1) >= w.min_range).sum()) for s in w.scans)
+    line = {"metric": "differentiable integration: points/s forward, forward+backward",
+            "value": valid / (tms / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "room 20 scans x 64x2048, 20 classes soft counts, loss = "
+                                   "sum D^2 + CE on 10k sampled voxels"},
+            "forward_ms": fms, "forward_backward_ms": tms, "backward_ms": tms - fms,
+            "memory": {"saved_for_backward": "inputs only; (voxel, point) pairs recomputed",
+                       "torch_peak_bytes_above_inputs": int(peak)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch(args):
+    """16 independent maps — 8 closed-set (64 beams, 20k-250k points per scan)
+    and 8 open-set (256-dim, 320x240 to 640x480 BF16) — one scan each per step,
+    integrated by one slim_integrate_batch call captured in a CUDA graph."""
+    import numpy as np
+    import torch
+    from paper_2512_12945_gb300 import build, slim, synth
+    build.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(5)
+    closed, opened = [], []
+    for k in range(8):
+        n_az = int(rng.integers(320, 3900))
+        closed.append(synth.street_lidar(seed=50 + k, n_scans=1, n_az=n_az))
+    sizes = [(320, 240), (400, 300), (480, 360), (640, 480)] * 2
+    for k, (wd, ht) in enumerate(sizes):
+        opened.append(synth.indoor_rgbd(seed=60 + k, n_frames=40, width=wd, height=ht, dim=256,
+                                        frames=[0]))
+    maps, items, valid = [], [], 0
+    for w in closed:
+        m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=20,
+                     min_range=w.min_range, max_range=w.max_range,
+                     body_from_sensor=w.body_from_sensor, max_points=262144,
+                     block_capacity=60000, hash_capacity=1 << 18)
+        maps.append(m)
+    for w in opened:
+        m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, mode="open", embed_dim=256,
+                     embed_storage="bf16", min_range=w.min_range, max_range=w.max_range,
+                     max_points=w.scans[0]["pts"].shape[0], voxel_capacity=1500000,
+                     block_capacity=60000, hash_capacity=1 << 18)
+        maps.append(m)
+    for m, w in zip(maps, closed + opened):
+        s = w.scans[0]
+        items.append((m, torch.from_numpy(s["pts"]).cuda(), s["pose"],
+                      torch.from_numpy(s["sem"]).cuda()))
+        valid += int((np.linalg.norm(s["pts"], axis=1) >= w.min_range).sum())
+    stream = torch.cuda.current_stream()
+
+    def eager():
+        for m in maps:
+            m.reset()
+        slim.slim_integrate_batch(items)
+
+    eager()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        eager()
+    ems = _timed(eager, args.steps, args.warmup, stream)
+    gms = _timed(graph.replay, args.steps, args.warmup, stream)
+    for m in maps:
+        m.sync()
+    line = {"metric": "batched points integrated/s (16 uneven maps, closed + open)",
+            "value": valid / (gms / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32 / bf16 storage",
+            "data": "synthetic",
+            "config": {"workload": "8 closed-set maps (64 beams x 320-3900 azimuths, 20 classes) "
+                                   "+ 8 open-set maps (256-dim, 320x240..640x480, bf16), one scan "
+                                   "each per step"},
+            "graph_ms_per_step": gms, "eager_ms_per_step": ems, "points_per_step": valid}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_room(args):
+    """The small room configuration: 10 scans of 16 x 512 (8,192 points)."""
+    import numpy as np
+    import torch
+    from paper_2512_12945_gb300 import build, slim, synth
+    build.build()
+    torch.cuda.set_device(0)
+    w = synth.room_lidar(seed=1, n_scans=10)
+    m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=10,
+                 min_range=w.min_range, max_range=w.max_range, max_points=8192)
+    pts = [torch.from_numpy(s["pts"]).cuda() for s in w.scans]
+    sem = [torch.from_numpy(s["sem"]).cuda() for s in w.scans]
+    items = [(m, p, s["pose"], q) for p, q, s in zip(pts, sem, w.scans)]
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        m.reset()
+        for p, q, s in zip(pts, sem, w.scans):
+            m.integrate(p, s["pose"], q)
+
+    def batched():
+        m.reset()
+        slim.slim_integrate_batch(items)
+
+    pms = _timed(plain, args.steps, args.warmup, stream)
+    bms = _timed(batched, args.steps, args.warmup, stream)
+    m.sync()
+    valid = sum(int((np.linalg.norm(s["pts"], axis=1) >= w.min_range).sum()) for s in w.scans)
+    line = {"metric": "points integrated/s (room, 10 scans x 16x512)", "value": valid / (bms / 1e3),
+            "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "room 10x10x3 m + 6 objects, 10 scans x 16x512, 10 classes"},
+            "plain_ms_per_step": pms, "batched_ms_per_step": bms}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "street":
+        return {"room": run_room, "indoor": run_indoor, "adjoint": run_adjoint,
+                "batch": run_batch}[args.workload](args)
     return run_ours(args)
 
 
