@@ -222,6 +222,10 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   mv.split = p->mode == SLIM_CLOSED_ONEHOT ? 1 : 0;
   if (m->mode != SLIM_OPEN) {
     if ((s = m->alloc(&mv.rec, bc * kBlockVoxels * (uint64_t)m->rs)) != SLIM_OK) return bail(s);
+    // the pool stays zero beyond the allocation counter (reset re-zeroes
+    // the used part), so kernels never zero a block they create
+    if (cudaMemset(mv.rec, 0, bc * kBlockVoxels * (uint64_t)m->rs * sizeof(float)) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "cudaMemset"));
   } else {
     const uint64_t rc = (uint64_t)p->voxel_capacity;
     const size_t esz = m->bf16 ? 2 : 4;
@@ -262,6 +266,8 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
     return bail(fail(SLIM_ERR_NOMEM, "cudaMallocHost failed"));
   }
   std::memset(m->pinned, 0, kNumCounters * sizeof(uint32_t));
+  if (cudaMemset(mv.ctr, 0, kNumCounters * sizeof(uint32_t)) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "cudaMemset"));
   cudaError_t e = cudaSuccess;
   if (m->mode != SLIM_OPEN) e = closed_setup_attributes(m->mode, m->K, m->tile_points);
   else {
@@ -287,6 +293,7 @@ slim_status slim_map_reset(slim_map* m, void* stream) {
   if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nh = (size_t)m->n_entries;
+  if (m->mode != SLIM_OPEN) SLIM_CUDA(launch_zero_used_blocks(m->mv, st));
   SLIM_CUDA(cudaMemsetAsync(m->mv.hkeys, 0xFF, nh * sizeof(uint64_t), st));
   SLIM_CUDA(cudaMemsetAsync(m->mv.hvals, 0xFF, nh * sizeof(uint32_t), st));
   SLIM_CUDA(cudaMemsetAsync(m->mv.ctr, 0, kNumCounters * sizeof(uint32_t), st));

@@ -1,20 +1,28 @@
 // Closed-set one-hot integration with shared-memory hash aggregation
-// (Sec. III-A TSDF + Sec. III-C / Theorem 1 Dirichlet counts), one kernel
-// per scan, one tile of TP points per CTA (TP = 64, 128 or 256 threads):
+// (Sec. III-A TSDF + Sec. III-C / Theorem 1 Dirichlet counts), one tile of
+// TP points per CTA (TP = 64, 128 or 256 threads), persistent over a batch
+// of scans:
 //   1. every thread loads its point and class probabilities first (the
 //      probability row as independent float4 loads, argmax afterwards), then
 //      marches the band; each kept pair is added at once into a tile-local
-//      table keyed by (tile block entry, local voxel, class) holding
-//      (count, sum d) — no pair list is staged and nothing is sorted;
-//   2. each distinct block of the tile is inserted into (or found in) the
-//      map's hash by its own thread; blocks this CTA creates are zeroed by
-//      the whole CTA, then published; only then does the CTA wait
-//      (time-bounded) for blocks other CTAs are still publishing, so no wait
-//      can be part of a cycle;
+//      table keyed by (tile block entry, local voxel, class). One 64-bit word
+//      per entry holds the key, the count and the sum of the pair's SDF in
+//      fixed point (units of tau / 2^20), so a pair costs one shared load and
+//      one shared atomic; no pair list is staged and nothing is sorted;
+//   2. each distinct block of the tile (compacted first) is inserted into
+//      (or found in) the map's hash by its own thread; a block this thread
+//      creates is published at once (its records are already zero: the pool
+//      is kept zero beyond the allocation counter, see k_zero_used_blocks);
+//      only then does the thread wait (time-bounded) for blocks other CTAs
+//      are still publishing, so no wait can be part of a cycle;
 //   3. flush: one vector red.add (S_k += sum d, c_k += count) per table
 //      entry into the voxel's class-split record (see common.cuh).
 // A pair whose table probe runs out is re-generated after the slots are
-// known and sent to HBM on its own.
+// known and sent to HBM on its own, in FP32.
+// Fixed point: a kept pair has d in [-tau, tau]; q = rint(d * 2^20 / tau)
+// is stored offset by 2^20 (so it is never negative), the rounding error is
+// at most tau * 2^-21 (+ one FP32 rounding of the scale) per pair, and the
+// tile sum (at most TP pairs per entry) is exact in the 30-bit field.
 #include "block_sort.cuh"
 #include "common.cuh"
 #include "geometry.cuh"
@@ -23,17 +31,19 @@
 
 namespace slim {
 
-constexpr uint32_t kVcEmpty = 0xFFFFFFFFu;
+constexpr unsigned long long kVcEmpty = ~0ull;
+constexpr int kVcKeyShift = 39;    // key: tile block entry << 15 | local << 6 | class
+constexpr int kVcCntShift = 30;    // count: 9 bits (at most TP <= 256 pairs per entry)
+constexpr uint32_t kQOne = 1u << 20;  // fixed-point unit of the SDF sum is tau / 2^20
 
 template <int TP>
 struct HashTile {
   static constexpr int kTbl = 4 * TP;    // block table entries (>= distinct blocks of a tile)
   static constexpr int kVc = 8 * TP;     // (voxel, class) accumulators
-  static constexpr int kNew = 4 * TP;    // blocks a tile may create
   static constexpr int kVcBits = kVc == 2048 ? 11 : (kVc == 1024 ? 10 : 9);
-  // tb_key u64 + tb_slot u32 per block entry, vc_key u32 + (sum, count) u64
-  // per accumulator, new-block list, counters
-  static constexpr size_t kSmem = (size_t)kTbl * 12 + (size_t)kVc * 12 + (size_t)kNew * 2 + 16 * 4;
+  // tb_key u64 + tb_slot u32 + compacted list u16 per block entry, one
+  // u64 per accumulator, counters
+  static constexpr size_t kSmem = (size_t)kTbl * 14 + (size_t)kVc * 8 + 16 * 4;
 };
 
 template <int TP>
@@ -67,34 +77,27 @@ __device__ __forceinline__ uint32_t htbl_find(const uint64_t* tb, uint64_t kb) {
   return 0xFFFFFFFFu;
 }
 
+// Add one pair (key, q) to the (voxel, class) table: claim an empty word
+// with the first observation, else add (1 count, q) to the word holding the
+// key. Returns false when the probe runs out.
 template <int TP>
-__device__ __forceinline__ int vc_insert(uint32_t* tbl, uint32_t key) {
+__device__ __forceinline__ bool vc_add(unsigned long long* tbl, uint32_t key, uint32_t q) {
   constexpr int N = HashTile<TP>::kVc;
+  const unsigned long long inc = (1ull << kVcCntShift) | (unsigned long long)q;
   uint32_t h = (key * 2654435761u) >> (32 - HashTile<TP>::kVcBits);
   for (int it = 0; it < 64; ++it) {
-    const uint32_t cur = *(volatile uint32_t*)&tbl[h];
-    if (cur == key) return (int)h;
+    unsigned long long cur = *(volatile unsigned long long*)&tbl[h];
     if (cur == kVcEmpty) {
-      const uint32_t prev = atomicCAS(&tbl[h], kVcEmpty, key);
-      if (prev == kVcEmpty || prev == key) return (int)h;
+      cur = atomicCAS(&tbl[h], kVcEmpty, ((unsigned long long)key << kVcKeyShift) | inc);
+      if (cur == kVcEmpty) return true;
+    }
+    if ((uint32_t)(cur >> kVcKeyShift) == key) {
+      atomicAdd(&tbl[h], inc);
+      return true;
     }
     h = (h + 1) & (N - 1);
   }
-  return -1;
-}
-
-// Accumulator word: FP32 sum in the high half, count in the low half; one
-// compare-and-swap adds an observation (exact FP32 addition, no fixed point).
-__device__ __forceinline__ void acc_add(unsigned long long* a, float d) {
-  unsigned long long cur = *(volatile unsigned long long*)a;
-  for (;;) {
-    const float s = __uint_as_float((uint32_t)(cur >> 32));
-    const unsigned long long nxt =
-        ((unsigned long long)__float_as_uint(__fadd_rn(s, d)) << 32) | ((cur & 0xFFFFFFFFull) + 1ull);
-    const unsigned long long prev = atomicCAS(a, cur, nxt);
-    if (prev == cur) return;
-    cur = prev;
-  }
+  return false;
 }
 
 __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
@@ -160,11 +163,10 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
                                                int tile_points, int64_t tile, unsigned char* sm) {
   using H = HashTile<TP>;
   uint64_t* tb_key = reinterpret_cast<uint64_t*>(sm);
-  unsigned long long* vc_acc = reinterpret_cast<unsigned long long*>(tb_key + H::kTbl);
-  uint32_t* tb_slot = reinterpret_cast<uint32_t*>(vc_acc + H::kVc);
-  uint32_t* vc_key = tb_slot + H::kTbl;
-  uint16_t* newe = reinterpret_cast<uint16_t*>(vc_key + H::kVc);
-  uint32_t* misc = reinterpret_cast<uint32_t*>(newe + H::kNew);
+  unsigned long long* vc = reinterpret_cast<unsigned long long*>(tb_key + H::kTbl);
+  uint32_t* tb_slot = reinterpret_cast<uint32_t*>(vc + H::kVc);
+  uint16_t* blist = reinterpret_cast<uint16_t*>(tb_slot + H::kTbl);
+  uint32_t* misc = reinterpret_cast<uint32_t*>(blist + H::kTbl);
 
   const int tid = threadIdx.x;
   // loads first: the point and its class probabilities
@@ -180,19 +182,18 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
   }
   if (tid == 0) {
     misc[0] = *(volatile uint32_t*)&mv.ctr[kCtrStatus];
-    misc[1] = 0;
-    misc[2] = 0;
+    misc[2] = 0;  // block table overflow
+    misc[3] = 0;  // distinct blocks
   }
-  for (int e = tid; e < H::kTbl; e += TP) tb_key[e] = kEmptyKey;
-  for (int e = tid; e < H::kVc / 4; e += TP) {
-    reinterpret_cast<uint4*>(vc_key)[e] = make_uint4(kVcEmpty, kVcEmpty, kVcEmpty, kVcEmpty);
-    reinterpret_cast<ulonglong2*>(vc_acc)[2 * e] = make_ulonglong2(0ull, 0ull);
-    reinterpret_cast<ulonglong2*>(vc_acc)[2 * e + 1] = make_ulonglong2(0ull, 0ull);
-  }
+  for (int e = tid; e < H::kTbl / 2; e += TP)
+    reinterpret_cast<ulonglong2*>(tb_key)[e] = make_ulonglong2(kEmptyKey, kEmptyKey);
+  for (int e = tid; e < H::kVc / 2; e += TP)
+    reinterpret_cast<ulonglong2*>(vc)[e] = make_ulonglong2(kVcEmpty, kVcEmpty);
   __syncthreads();
   if (misc[0]) return;
 
   // 1. band DDA, aggregating every pair into the (voxel, class) table
+  const float qscale = __fdiv_rn(1048576.0f, g.tau);
   int ovf = -1;  // index of the first pair the table could not take
   Ray ry;
   const bool valid = mine && ray_setup(g, p0, p1, p2, ry);
@@ -211,12 +212,9 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
       const int idx = k++;
       if (last_tb == 0xFFFFFFFFu || ovf >= 0) return;
       const uint32_t key = (last_tb << 15) | ((uint32_t)local_index(i0, i1, i2) << 6) | cls;
-      const int e = vc_insert<TP>(vc_key, key);
-      if (e < 0) {
-        ovf = idx;
-        return;
-      }
-      acc_add(&vc_acc[e], d);
+      int qi = __float2int_rn(__fmul_rn(d, qscale));
+      qi = max(-(int)kQOne, min((int)kQOne, qi));
+      if (!vc_add<TP>(vc, key, (uint32_t)(qi + (int)kQOne))) ovf = idx;
     });
   }
   __syncthreads();
@@ -224,17 +222,30 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
     if (tid == 0) raise_status(mv.ctr, kDevInternal, 4);
     return;
   }
+  // compact the occupied block-table entries
+#pragma unroll
+  for (int q = 0; q < H::kTbl / TP; ++q) {
+    const int e = tid + q * TP;
+    const bool occ = tb_key[e] != kEmptyKey;
+    const unsigned b = __ballot_sync(0xFFFFFFFFu, occ);
+    uint32_t base = 0;
+    if (lane_id() == 0 && b) base = atomicAdd(&misc[3], (uint32_t)__popc(b));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (occ) blist[base + __popc(b & ((1u << lane_id()) - 1u))] = (uint16_t)e;
+  }
+  __syncthreads();
+  const int nblk = (int)misc[3];
 
-  // 2. insert-or-find each distinct block (table entries tid + TP q)
+  // 2. insert-or-find each distinct block (compacted items tid + TP q); a
+  // created block is published at once, then blocks other CTAs created are
+  // resolved (acquire: the slot read orders this CTA's reductions after it)
   constexpr int Q = H::kTbl / TP;
-  uint32_t hpos[Q];
-  uint32_t created = 0;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const int e = tid + q * TP;
+    const int i = tid + q * TP;
+    if (i >= nblk) break;
+    const int e = blist[i];
     const uint64_t key = tb_key[e];
-    hpos[q] = 0;
-    if (key == kEmptyKey) continue;
     uint32_t h = entry_of(mv, key);
     int state = -1;
     for (int pr = 0; pr < mv.max_probe; ++pr) {
@@ -258,75 +269,47 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
       }
       h = (h + 1) & mv.entry_mask;
     }
-    hpos[q] = h;
+    uint32_t v = kFailSlot;
     if (state < 0) {
       raise_status(mv.ctr, kDevCapacity, 2);
-      tb_slot[e] = kFailSlot;
     } else if (state == 1) {
       const uint32_t slot = atomicAdd(&mv.ctr[kCtrBlocks], 1u);
-      const uint32_t ni = slot < mv.block_cap ? atomicAdd(&misc[1], 1u) : 0u;
-      if (slot >= mv.block_cap || ni >= (uint32_t)H::kNew) {
-        raise_status(mv.ctr, slot >= mv.block_cap ? kDevCapacity : kDevInternal, 1);
-        st_release(&mv.hvals[h], kFailSlot);
-        tb_slot[e] = kFailSlot;
+      if (slot >= mv.block_cap) {
+        raise_status(mv.ctr, kDevCapacity, 1);
       } else {
         mv.blk_key[slot] = key;
-        tb_slot[e] = slot;
-        newe[ni] = (uint16_t)e;
-        created |= 1u << q;
+        v = slot;
       }
+      st_release(&mv.hvals[h], v);
     } else {
-      tb_slot[e] = kNoSlot;
-    }
-  }
-  __syncthreads();
-  // zero the blocks this CTA created, then publish them: every thread fences
-  // its own zero stores (a fence orders only the issuing thread's writes)
-  // before the barrier, so the slot is published after all of them
-  const uint32_t nnew = min(misc[1], (uint32_t)H::kNew);
-  if (nnew) {
-    for (uint32_t i = 0; i < nnew; ++i) {
-      float4* p = reinterpret_cast<float4*>(mv.rec + (size_t)tb_slot[newe[i]] * kBlockVoxels * mv.rs);
-      const int n4 = kBlockVoxels * mv.rs / 4;
-      for (int k = tid; k < n4; k += TP) p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    __threadfence();
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-      if (created & (1u << q)) st_release(&mv.hvals[hpos[q]], tb_slot[tid + q * TP]);
-  }
-  // resolve the blocks other CTAs created (acquire: their zeroing is visible
-  // before this CTA's reductions, which depend on the slot read here)
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int e = tid + q * TP;
-    if (tb_key[e] == kEmptyKey || tb_slot[e] != kNoSlot) continue;
-    uint32_t* hv = &mv.hvals[hpos[q]];
-    uint32_t v = ld_acquire(hv);
-    if (v == kNoSlot) {
-      const uint64_t t0 = global_ns();
-      while ((v = ld_acquire(hv)) == kNoSlot) {
-        if (global_ns() - t0 > kCrossCtaWaitNs) {
-          raise_status(mv.ctr, kDevTimeout, 5);
-          v = kFailSlot;
-          break;
+      uint32_t* hv = &mv.hvals[h];
+      v = ld_acquire(hv);
+      if (v == kNoSlot) {
+        const uint64_t t0 = global_ns();
+        while ((v = ld_acquire(hv)) == kNoSlot) {
+          if (global_ns() - t0 > kCrossCtaWaitNs) {
+            raise_status(mv.ctr, kDevTimeout, 5);
+            v = kFailSlot;
+            break;
+          }
+          __nanosleep(100);
         }
-        __nanosleep(100);
       }
-    }
-    if (v != kFailSlot && v >= mv.block_cap) {  // consistency check, never expected
-      raise_status(mv.ctr, kDevInternal, 9);
-      v = kFailSlot;
+      if (v != kFailSlot && v >= mv.block_cap) {  // consistency check, never expected
+        raise_status(mv.ctr, kDevInternal, 9);
+        v = kFailSlot;
+      }
     }
     tb_slot[e] = v;
   }
   __syncthreads();
 
   // 3. flush: one vector red.add (S_k, c_k) per entry
+  const float qunit = __fmul_rn(g.tau, 1.0f / 1048576.0f);  // exact: a power-of-two scale
   for (int e = tid; e < H::kVc; e += TP) {
-    const uint32_t key = vc_key[e];
-    if (key == kVcEmpty) continue;
+    const unsigned long long w = vc[e];
+    if (w == kVcEmpty) continue;
+    const uint32_t key = (uint32_t)(w >> kVcKeyShift);
     if ((key >> 15) >= (uint32_t)H::kTbl) {  // consistency check, never expected
       raise_status(mv.ctr, kDevInternal, 6);
       continue;
@@ -337,9 +320,11 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
       raise_status(mv.ctr, kDevInternal, 7);
       continue;
     }
+    const uint32_t cnt = (uint32_t)(w >> kVcCntShift) & 511u;
+    const int32_t qs = (int32_t)(uint32_t)(w & ((1ull << kVcCntShift) - 1ull)) -
+                       (int32_t)(cnt * kQOne);
     float* r = mv.rec + ((size_t)slot * kBlockVoxels + ((key >> 6) & 511u)) * mv.rs;
-    const unsigned long long a = vc_acc[e];
-    red_add_v2(r + 2 * (key & 63u), __uint_as_float((uint32_t)(a >> 32)), (float)(uint32_t)a);
+    red_add_v2(r + 2 * (key & 63u), __fmul_rn((float)qs, qunit), (float)cnt);
   }
 
   // 4. pairs the table could not take go to HBM one by one
@@ -417,6 +402,26 @@ cudaError_t hash_setup_attributes() {
   if (e == cudaSuccess) e = setup_one<128>(1);
   if (e == cudaSuccess) e = setup_one<256>(2);
   return e;
+}
+
+// Keeps the record pool zero beyond the allocation counter: zeroes the
+// records of blocks [0, min(allocated, capacity)) so that a reset map hands
+// out zeroed blocks (the pool is zeroed once when the map is created).
+__global__ void __launch_bounds__(256) k_zero_used_blocks(float4* rec, const uint32_t* ctr,
+                                                          uint32_t block_cap, int rs) {
+  const uint32_t nb = min(*(volatile const uint32_t*)&ctr[kCtrBlocks], block_cap);
+  const size_t n4 = (size_t)nb * kBlockVoxels * (size_t)rs / 4;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (size_t)gridDim.x * blockDim.x)
+    rec[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+cudaError_t launch_zero_used_blocks(const MapView& mv, cudaStream_t st) {
+  if (!mv.rec) return cudaSuccess;
+  const int sms = g_sms > 0 ? g_sms : 152;
+  k_zero_used_blocks<<<(unsigned)(sms * 8), 256, 0, st>>>(reinterpret_cast<float4*>(mv.rec), mv.ctr,
+                                                       mv.block_cap, mv.rs);
+  return cudaGetLastError();
 }
 
 // Largest number of points a TP-thread tile may hold: its distinct blocks

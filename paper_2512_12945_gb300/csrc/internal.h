@@ -37,6 +37,8 @@ struct HashBatch {
 };
 cudaError_t launch_hash_batch(HashBatch& b, int tile, int ctas_per_sm, cudaStream_t st);
 cudaError_t hash_setup_attributes();
+// Zero the records of the blocks allocated so far (closed-set maps).
+cudaError_t launch_zero_used_blocks(const MapView& mv, cudaStream_t st);
 cudaError_t launch_fuse_hash(const MapView& mv, const ScanGeom& g, const float* pts,
                              const float* sem, int64_t n, int K, int tile, int band_blocks,
                              cudaStream_t st);
