@@ -117,7 +117,10 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out);
 slim_status slim_map_destroy(slim_map* m);
 
 /* Empty the map (all blocks and voxels gone, status cleared), keeping its
- * memory. Queued on `stream`. */
+ * memory. Queued on `stream`. For closed-set maps it also re-zeroes the
+ * records of the blocks allocated so far (one kernel, SLIM_KERNEL_RESET):
+ * the record pool is kept zero beyond the allocation counter, so
+ * integration never zeroes a block it creates. */
 slim_status slim_map_reset(slim_map* m, void* stream);
 
 /* Integrate one scan (Sec. III-A to III-D). For each of the n points:
@@ -263,6 +266,7 @@ typedef enum {
   SLIM_KERNEL_QUERY = 4,        /* tensor-core query GEMM + epilogue */
   SLIM_KERNEL_BACKWARD = 5,     /* adjoint gather */
   SLIM_KERNEL_BATCH = 6,        /* batched persistent integration */
+  SLIM_KERNEL_RESET = 7,        /* slim_map_reset: re-zeroing of used closed-set blocks */
   SLIM_KERNEL_KINDS = 8
 } slim_kernel;
 

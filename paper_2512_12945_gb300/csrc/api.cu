@@ -293,7 +293,11 @@ slim_status slim_map_reset(slim_map* m, void* stream) {
   if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nh = (size_t)m->n_entries;
-  if (m->mode != SLIM_OPEN) SLIM_CUDA(launch_zero_used_blocks(m->mv, st));
+  if (m->mode != SLIM_OPEN) {
+    const int tok = prof_begin(m, SLIM_KERNEL_RESET, st);
+    SLIM_CUDA(launch_zero_used_blocks(m->mv, st));
+    prof_end(m, tok, st);
+  }
   SLIM_CUDA(cudaMemsetAsync(m->mv.hkeys, 0xFF, nh * sizeof(uint64_t), st));
   SLIM_CUDA(cudaMemsetAsync(m->mv.hvals, 0xFF, nh * sizeof(uint32_t), st));
   SLIM_CUDA(cudaMemsetAsync(m->mv.ctr, 0, kNumCounters * sizeof(uint32_t), st));

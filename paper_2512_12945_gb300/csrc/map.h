@@ -19,7 +19,8 @@ struct OpenScratch {
   uint32_t* vals_tmp = nullptr;
   float* pair_d = nullptr;       // SDF of each pair, by pair index
   uint32_t* pair_pt = nullptr;   // point of each pair, by pair index
-  uint32_t* seg_start = nullptr; // first sorted position of each voxel run
+  float2* part = nullptr;        // per piece and side: (mean, M2) per element
+  uint4* meta = nullptr;         // per piece and side: (n, sum d, flags, key)
   uint32_t* ctr = nullptr;       // device counters: pairs, runs
   void* tmp = nullptr;           // sort / scan temp
 };

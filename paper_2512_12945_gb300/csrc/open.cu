@@ -6,19 +6,22 @@
 //   zbar = batch mean,  M2 = sum (z - zbar)^2,  W' = W + n,
 //   m'    = (W m + n zbar) / W'            = m + (zbar - m) n / W'
 //   beta' = beta + M2 / 2 + (W n / W') (zbar - m)^2 / 2.
-// zbar and M2 are accumulated about the batch's first observation s
-// (S1 = sum (z - s), S2 = sum (z - s)^2, zbar = s + S1 / n,
-// M2 = S2 - S1^2 / n), which keeps the sums small and free of cancellation.
+// zbar and M2 of a run of observations are accumulated about its first
+// observation s (S1 = sum (z - s), S2 = sum (z - s)^2, zbar = s + S1 / n,
+// M2 = S2 - S1^2 / n), which keeps the sums small and free of cancellation;
+// runs longer than one piece are merged from per-piece statistics.
 //
 // Pipeline per scan (besides the shared block-allocation pass):
 //   k_open_pairs  band DDA per point; the point's distinct blocks are looked
 //                 up warp-cooperatively; every (voxel, point) pair is written
 //                 as key = slot << 9 | local, with its d and point index.
 //   radix sort    device-wide, by voxel key (count of pairs read on device).
-//   k_open_heads  segment starts (first pair of each voxel run).
-//   k_open_apply  one warp per voxel run: exclusive owner of the voxel, so
-//                 the state is read once, updated in FP32 registers and
-//                 written once (f32 or bf16 storage), no atomics on records.
+//   k_open_frag   one warp per piece of 64 sorted pairs: whole runs are
+//                 applied at once (the warp owns the voxel: state read once,
+//                 updated in FP32 registers, written once, f32 or bf16
+//                 storage, no atomics on records); runs cut by a piece
+//                 boundary leave per-piece statistics.
+//   k_open_merge  one warp per cut run: merge its pieces and apply.
 #include <cuda_bf16.h>
 
 #include "block_sort.cuh"
@@ -30,7 +33,7 @@ namespace slim {
 
 constexpr int kOpenBandBlocks = 8;
 // device counters of the open-set scratch
-enum { kOpPairs = 0, kOpSegs = 1, kOpCounters = 4 };
+enum { kOpPairs = 0, kOpCounters = 4 };
 
 __global__ void __launch_bounds__(256) k_open_pairs(MapView mv, ScanGeom g,
                                                     const float* __restrict__ pts, int64_t n,
@@ -113,36 +116,6 @@ __global__ void __launch_bounds__(256) k_open_pairs(MapView mv, ScanGeom g,
   }
 }
 
-// First pair of every run of equal keys -> seg_start (order irrelevant).
-__global__ void __launch_bounds__(256) k_open_heads(const uint32_t* __restrict__ keys,
-                                                    uint32_t* ctr, uint32_t* seg_start,
-                                                    int64_t n_max) {
-  const int64_t n = min(n_max, (int64_t)ctr[kOpPairs]);
-  const unsigned lane = lane_id();
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = b + threadIdx.x;
-    bool head = false;
-    if (i < n) {
-      const uint32_t k = keys[i];
-      head = k != 0xFFFFFFFFu && (i == 0 || keys[i - 1] != k);
-    }
-    const unsigned hm = __ballot_sync(0xFFFFFFFFu, head);
-    uint32_t base = 0;
-    if (lane == 0 && hm) base = atomicAdd(&ctr[kOpSegs], (uint32_t)__popc(hm));
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (head) seg_start[base + __popc(hm & ((1u << lane) - 1u))] = (uint32_t)i;
-  }
-}
-
-// s += y with the rounding error carried in c (Kahan); explicit _rn ops
-// keep the compiler from contracting or reassociating them.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float y) {
-  const float yc = __fsub_rn(y, c);
-  const float t = __fadd_rn(s, yc);
-  c = __fsub_rn(__fsub_rn(t, s), yc);
-  s = t;
-}
-
 template <int BF16>
 __device__ __forceinline__ float4 load4(const void* base, size_t idx) {
   if (BF16) {
@@ -169,111 +142,311 @@ __device__ __forceinline__ void store4(void* base, size_t idx, float4 v) {
   }
 }
 
-// One warp per voxel run. Lane q holds elements [4q, 4q + 4) of each
-// 128-element chunk of the embedding.
+// ---------------------------------------------------------------- apply
+// Sorted pairs are cut into pieces of kPiece consecutive pairs, one warp per
+// piece. A piece holds fragments (maximal runs of one voxel key). A fragment
+// that is a whole run is applied at once by its warp (exclusive owner of the
+// voxel for this scan). A fragment cut by a piece boundary leaves its
+// statistics (n, sum d, per element mean and M2) in a side slot of its
+// piece: side 0 for the fragment that began in an earlier piece, side 1 for
+// the fragment that goes on into the next one. k_open_merge then takes, for
+// every run that starts in a piece p and leaves it, the side-1 slot of p and
+// the side-0 slots of the following pieces up to the run's end, merges them
+// with the pairwise update of Chan, Golub and LeVeque (count, mean, M2;
+// compensated sums) and applies the run. No warp walks more than kPiece
+// observations, however many pixels a voxel collects in one frame.
+constexpr int kPiece = 64;
+enum { kFragValid = 1, kFragHead = 2, kFragEnd = 4 };
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, off);
+  return x;
+}
+
+// Point index of piece position k (lane k & 31 of pt0 / pt1).
+__device__ __forceinline__ uint32_t piece_pt(uint32_t pt0, uint32_t pt1, int k) {
+  return __shfl_sync(0xFFFFFFFFu, k < 32 ? pt0 : pt1, k & 31);
+}
+
+__device__ __forceinline__ float4 sem4(const float* __restrict__ sem, uint32_t pt, int L, int e,
+                                       bool on) {
+  return on ? *reinterpret_cast<const float4*>(sem + (size_t)pt * L + e)
+            : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Batch mean and M2 of one fragment [fb, fe) for elements [e, e + 4),
+// accumulated about the fragment's first observation (S1 = sum (z - s),
+// S2 = sum (z - s)^2, mean = s + S1 / n, M2 = S2 - S1^2 / n).
+__device__ __forceinline__ void frag_stats(const float* __restrict__ sem, int L, uint32_t pt0,
+                                           uint32_t pt1, int fb, int fe, int e, bool on,
+                                           float mean[4], float m2[4]) {
+  const float4 s4 = sem4(sem, piece_pt(pt0, pt1, fb), L, e, on);
+  const float sh[4] = {s4.x, s4.y, s4.z, s4.w};
+  float s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
+  int k = fb + 1;
+  for (; k + 3 < fe; k += 4) {
+    float4 z[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) z[u] = sem4(sem, piece_pt(pt0, pt1, k + u), L, e, on);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float zv[4] = {z[u].x, z[u].y, z[u].z, z[u].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float y = __fsub_rn(zv[q], sh[q]);
+        s1[q] = __fadd_rn(s1[q], y);
+        s2[q] = __fadd_rn(s2[q], __fmul_rn(y, y));
+      }
+    }
+  }
+  for (; k < fe; ++k) {
+    const float4 z = sem4(sem, piece_pt(pt0, pt1, k), L, e, on);
+    const float zv[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float y = __fsub_rn(zv[q], sh[q]);
+      s1[q] = __fadd_rn(s1[q], y);
+      s2[q] = __fadd_rn(s2[q], __fmul_rn(y, y));
+    }
+  }
+  const float invn = __fdiv_rn(1.0f, (float)(fe - fb));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    mean[q] = __fadd_rn(sh[q], __fmul_rn(s1[q], invn));
+    m2[q] = fmaxf(__fsub_rn(s2[q], __fmul_rn(__fmul_rn(s1[q], s1[q]), invn)), 0.f);
+  }
+}
+
+// Voxel row of key (slot << 9 | local), allocated on its first observation
+// by lane 0 (the calling warp owns the voxel for this scan); -1 on a
+// capacity fault.
+__device__ __forceinline__ int32_t voxel_row(const MapView& mv, uint32_t key, int* fresh) {
+  int32_t row = 0;
+  int fr = 0;
+  if (lane_id() == 0) {
+    int32_t* vr = mv.vox_row + (size_t)(key >> 9) * kBlockVoxels + (key & 511u);
+    row = *vr;
+    if (row < 0) {
+      const uint32_t r = atomicAdd(&mv.ctr[kCtrRows], 1u);
+      if (r >= mv.row_cap) {
+        raise_status(mv.ctr, kDevCapacity, 12);
+        row = -1;
+      } else {
+        row = (int32_t)r;
+        *vr = row;
+        fr = 1;
+      }
+    }
+  }
+  *fresh = __shfl_sync(0xFFFFFFFFu, fr, 0);
+  return __shfl_sync(0xFFFFFFFFu, row, 0);
+}
+
+// Theorem 2 update of elements [e, e + 4) of a row with the batch
+// statistics: m' = m + (zbar - m) n / W', beta' = beta + M2 / 2 +
+// (W n / W') (zbar - m)^2 / 2 (fm = n / W', fb = W n / W'). Returns the
+// partial |m'|^2 of the stored values.
 template <int BF16>
-__global__ void __launch_bounds__(256) k_open_apply(MapView mv, const uint32_t* __restrict__ keys,
-                                                    const uint32_t* __restrict__ vals,
-                                                    const float* __restrict__ pair_d,
-                                                    const uint32_t* __restrict__ pair_pt,
-                                                    const uint32_t* __restrict__ seg_start,
-                                                    const uint32_t* __restrict__ ctr,
-                                                    const float* __restrict__ sem, int L,
-                                                    int64_t n_max) {
+__device__ __forceinline__ float nig_apply4(const MapView& mv, size_t rbase, int e, int fresh,
+                                            float fm, float fb, const float mean[4],
+                                            const float m2[4]) {
+  float4 m = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : load4<BF16>(mv.mrow, rbase + e);
+  float4 b = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : load4<BF16>(mv.brow, rbase + e);
+  float mv4[4] = {m.x, m.y, m.z, m.w}, bv4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float d = mean[q] - mv4[q];
+    bv4[q] += 0.5f * (m2[q] + fb * d * d);
+    mv4[q] += d * fm;
+  }
+  m = make_float4(mv4[0], mv4[1], mv4[2], mv4[3]);
+  b = make_float4(bv4[0], bv4[1], bv4[2], bv4[3]);
+  store4<BF16>(mv.mrow, rbase + e, m);
+  store4<BF16>(mv.brow, rbase + e, b);
+  if (BF16) m = load4<BF16>(mv.mrow, rbase + e);  // norm of the stored values
+  return m.x * m.x + m.y * m.y + m.z * m.z + m.w * m.w;
+}
+
+template <int BF16>
+__global__ void __launch_bounds__(256) k_open_frag(MapView mv, const uint32_t* __restrict__ keys,
+                                                   const uint32_t* __restrict__ vals,
+                                                   const float* __restrict__ pair_d,
+                                                   const uint32_t* __restrict__ pair_pt,
+                                                   const uint32_t* __restrict__ ctr,
+                                                   const float* __restrict__ sem, int L,
+                                                   int64_t n_max, float2* part, uint4* meta) {
   if (*(volatile uint32_t*)&mv.ctr[kCtrStatus]) return;
   const unsigned lane = lane_id();
   const int64_t n = min(n_max, (int64_t)ctr[kOpPairs]);
-  const uint32_t nseg = ctr[kOpSegs];
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nseg; s += warps) {
-    const int64_t start = seg_start[s];
-    const uint32_t key = keys[start];
-    // run end: first differing key
-    int64_t end = n;
-    for (int64_t b = start + 1; b < n; b += 32) {
-      const int64_t i = b + lane;
-      const bool diff = i < n && keys[i] != key;
-      const unsigned dm = __ballot_sync(0xFFFFFFFFu, diff);
-      if (dm) {
-        end = b + __ffs(dm) - 1;
-        break;
-      }
-      if (b + 32 >= n) break;
-    }
-    const uint32_t slot = key >> 9, local = key & 511u;
-    int32_t row = 0;
-    int fresh = 0;
-    if (lane == 0) {
-      int32_t* vr = mv.vox_row + (size_t)slot * kBlockVoxels + local;
-      row = *vr;
-      if (row < 0) {
-        const uint32_t r = atomicAdd(&mv.ctr[kCtrRows], 1u);
-        if (r >= mv.row_cap) {
-          raise_status(mv.ctr, kDevCapacity, 12);
-          row = -1;
-        } else {
-          row = (int32_t)r;
-          *vr = row;
-          fresh = 1;
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t base = p * kPiece;
+  if (base >= n) return;
+  const int m = (int)(n - base < kPiece ? n - base : (int64_t)kPiece);
+  constexpr uint32_t kInv = 0xFFFFFFFFu;
+  const int64_t i0 = base + lane, i1 = base + 32 + lane;
+  const uint32_t key0 = (int)lane < m ? keys[i0] : kInv;
+  const uint32_t key1 = 32 + (int)lane < m ? keys[i1] : kInv;
+  uint32_t pt0 = 0, pt1 = 0;
+  float d0 = 0.f, d1 = 0.f;
+  if (key0 != kInv) {
+    const uint32_t v = vals[i0];
+    pt0 = pair_pt[v];
+    d0 = pair_d[v];
+  }
+  if (key1 != kInv) {
+    const uint32_t v = vals[i1];
+    pt1 = pair_pt[v];
+    d1 = pair_d[v];
+  }
+  const uint32_t prev_key = base > 0 ? keys[base - 1] : kInv;
+  const uint32_t next_key = base + kPiece < n ? keys[base + kPiece] : kInv;
+  // fragment starts as a 64-bit mask over the piece positions
+  const uint32_t up0 = __shfl_up_sync(0xFFFFFFFFu, key0, 1);
+  const uint32_t up1 = __shfl_up_sync(0xFFFFFFFFu, key1, 1);
+  const uint32_t last0 = __shfl_sync(0xFFFFFFFFu, key0, 31);
+  const bool st0 = lane == 0 || key0 != up0;
+  const bool st1 = lane == 0 ? key1 != last0 : key1 != up1;
+  const uint64_t smask = (uint64_t)__ballot_sync(0xFFFFFFFFu, st0) |
+                         ((uint64_t)__ballot_sync(0xFFFFFFFFu, st1) << 32);
+  if (lane == 0) meta[2 * p + 1] = make_uint4(0u, 0u, 0u, 0u);
+  int fb = 0;
+  while (fb < m) {
+    const uint64_t rest = fb < 63 ? (smask >> (fb + 1)) << (fb + 1) : 0ull;
+    const int fe = rest ? min(m, __ffsll((long long)rest) - 1) : m;
+    const uint32_t key = __shfl_sync(0xFFFFFFFFu, fb < 32 ? key0 : key1, fb & 31);
+    if (key == kInv) break;  // pairs without a block sort last
+    const bool before = fb == 0 && prev_key == key;
+    const bool after = fe == kPiece && next_key == key;
+    float sd = 0.f;
+    if ((int)lane >= fb && (int)lane < fe) sd += d0;
+    if (32 + (int)lane >= fb && 32 + (int)lane < fe) sd += d1;
+    sd = warp_sum(sd);
+    const int nf = fe - fb;
+    if (!before && !after) {  // a whole run: apply now
+      int fresh = 0;
+      const int32_t row = voxel_row(mv, key, &fresh);
+      if (row >= 0) {
+        const float2 sw = fresh ? make_float2(0.f, 0.f) : mv.tsdf[row];
+        const float Wn = sw.y + (float)nf;
+        const float fm = (float)nf / Wn, fbw = sw.y * (float)nf / Wn;
+        const size_t rbase = (size_t)row * L;
+        float nrm = 0.f;
+        for (int c0 = 0; c0 < L; c0 += 128) {
+          const int e = c0 + 4 * (int)lane;
+          const bool on = e < L;
+          float mean[4], m2[4];
+          frag_stats(sem, L, pt0, pt1, fb, fe, e, on, mean, m2);
+          if (on) nrm += nig_apply4<BF16>(mv, rbase, e, fresh, fm, fbw, mean, m2);
+        }
+        nrm = warp_sum(nrm);
+        if (lane == 0) {
+          mv.tsdf[row] = make_float2(sw.x + sd, Wn);
+          mv.mnorm2[row] = nrm;
         }
       }
+    } else {  // cut by a piece boundary: leave the statistics for the merge
+      const int side = before ? 0 : 1;
+      const uint32_t flags = kFragValid | (before ? 0u : (uint32_t)kFragHead) |
+                             (after ? 0u : (uint32_t)kFragEnd);
+      float2* dst = part + (size_t)(2 * p + side) * L;
+      for (int c0 = 0; c0 < L; c0 += 128) {
+        const int e = c0 + 4 * (int)lane;
+        const bool on = e < L;
+        float mean[4], m2[4];
+        frag_stats(sem, L, pt0, pt1, fb, fe, e, on, mean, m2);
+        if (on) {
+          float4* d4 = reinterpret_cast<float4*>(dst + e);
+          d4[0] = make_float4(mean[0], m2[0], mean[1], m2[1]);
+          d4[1] = make_float4(mean[2], m2[2], mean[3], m2[3]);
+        }
+      }
+      if (lane == 0) meta[2 * p + side] = make_uint4((uint32_t)nf, __float_as_uint(sd), flags, key);
     }
-    row = __shfl_sync(0xFFFFFFFFu, row, 0);
-    fresh = __shfl_sync(0xFFFFFFFFu, fresh, 0);
+    fb = fe;
+  }
+}
+
+// One warp per run that leaves the piece it starts in: merge its fragments
+// (side 1 of the head piece, side 0 of the following pieces up to the
+// fragment flagged as the run's end) and apply the run.
+template <int BF16>
+__global__ void __launch_bounds__(256) k_open_merge(MapView mv, const uint32_t* __restrict__ ctr,
+                                                    int L, int64_t n_max,
+                                                    const float2* __restrict__ part,
+                                                    const uint4* __restrict__ meta) {
+  if (*(volatile uint32_t*)&mv.ctr[kCtrStatus]) return;
+  const unsigned lane = lane_id();
+  const int64_t n = min(n_max, (int64_t)ctr[kOpPairs]);
+  const int64_t np = (n + kPiece - 1) / kPiece;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < np; p += warps) {
+    const uint4 h = meta[2 * p + 1];
+    if (!(h.z & kFragHead)) continue;
+    const uint32_t key = h.w;
+    // the chain of pieces: count, sum d and its end
+    float ntot = (float)h.x, sd = __uint_as_float(h.y);
+    int64_t q = p + 1;
+    bool ok = false;
+    for (; q < np; ++q) {
+      const uint4 t = meta[2 * q];
+      if (!(t.z & kFragValid) || t.w != key) break;
+      ntot += (float)t.x;
+      sd += __uint_as_float(t.y);
+      if (t.z & kFragEnd) {
+        ok = true;
+        break;
+      }
+    }
+    if (!ok) {  // consistency check, never expected
+      if (lane == 0) raise_status(mv.ctr, kDevInternal, 13);
+      continue;
+    }
+    const int64_t q_end = q;
+    int fresh = 0;
+    const int32_t row = voxel_row(mv, key, &fresh);
     if (row < 0) continue;
-    const float cnt = (float)(end - start);
-    // sum of d over the run
-    float sd = 0.f;
-    for (int64_t i = start + lane; i < end; i += 32) sd += pair_d[vals[i]];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sd += __shfl_xor_sync(0xFFFFFFFFu, sd, off);
     const float2 sw = fresh ? make_float2(0.f, 0.f) : mv.tsdf[row];
-    const float Wn = sw.y + cnt;
-    const float invn = 1.0f / cnt;
-    const float fm = cnt / Wn;              // n / W'
-    const float fb = sw.y * cnt / Wn;       // W n / W'
+    const float Wn = sw.y + ntot;
+    const float fm = ntot / Wn, fbw = sw.y * ntot / Wn;
     const size_t rbase = (size_t)row * L;
-    const float* zfirst = sem + (size_t)pair_pt[vals[start]] * L;
     float nrm = 0.f;
     for (int c0 = 0; c0 < L; c0 += 128) {
       const int e = c0 + 4 * (int)lane;
       if (e >= L) continue;
-      const float4 sh = *reinterpret_cast<const float4*>(zfirst + e);
-      // compensated (Kahan) sums: a voxel may collect thousands of
-      // observations in one depth frame
-      float s1a[4] = {0.f, 0.f, 0.f, 0.f}, s1c[4] = {0.f, 0.f, 0.f, 0.f};
-      float s2a[4] = {0.f, 0.f, 0.f, 0.f}, s2c[4] = {0.f, 0.f, 0.f, 0.f};
-      const float shv[4] = {sh.x, sh.y, sh.z, sh.w};
-      for (int64_t i = start; i < end; ++i) {
-        const uint32_t pt = pair_pt[vals[i]];
-        const float4 z = *reinterpret_cast<const float4*>(sem + (size_t)pt * L + e);
-        const float zv[4] = {z.x, z.y, z.z, z.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float y = __fsub_rn(zv[q], shv[q]);
-          kahan_add(s1a[q], s1c[q], y);
-          kahan_add(s2a[q], s2c[q], __fmul_rn(y, y));
-        }
+      float na = (float)h.x;
+      float mean[4], m2[4], mc[4] = {0.f, 0.f, 0.f, 0.f}, vc[4] = {0.f, 0.f, 0.f, 0.f};
+      {
+        const float4* s4 = reinterpret_cast<const float4*>(part + (size_t)(2 * p + 1) * L + e);
+        const float4 a = s4[0], b = s4[1];
+        mean[0] = a.x; m2[0] = a.y; mean[1] = a.z; m2[1] = a.w;
+        mean[2] = b.x; m2[2] = b.y; mean[3] = b.z; m2[3] = b.w;
       }
-      const float4 s1 = make_float4(s1a[0], s1a[1], s1a[2], s1a[3]);
-      const float4 s2 = make_float4(s2a[0], s2a[1], s2a[2], s2a[3]);
-      float4 m = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : load4<BF16>(mv.mrow, rbase + e);
-      float4 b = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : load4<BF16>(mv.brow, rbase + e);
-      const float zb0 = sh.x + s1.x * invn, zb1 = sh.y + s1.y * invn;
-      const float zb2 = sh.z + s1.z * invn, zb3 = sh.w + s1.w * invn;
-      const float d0 = zb0 - m.x, d1 = zb1 - m.y, d2 = zb2 - m.z, d3 = zb3 - m.w;
-      b.x += 0.5f * ((s2.x - s1.x * s1.x * invn) + fb * d0 * d0);
-      b.y += 0.5f * ((s2.y - s1.y * s1.y * invn) + fb * d1 * d1);
-      b.z += 0.5f * ((s2.z - s1.z * s1.z * invn) + fb * d2 * d2);
-      b.w += 0.5f * ((s2.w - s1.w * s1.w * invn) + fb * d3 * d3);
-      m.x += d0 * fm; m.y += d1 * fm; m.z += d2 * fm; m.w += d3 * fm;
-      store4<BF16>(mv.mrow, rbase + e, m);
-      store4<BF16>(mv.brow, rbase + e, b);
-      if (BF16) m = load4<BF16>(mv.mrow, rbase + e);  // norm of the stored values
-      nrm += m.x * m.x + m.y * m.y + m.z * m.z + m.w * m.w;
-    }
+      for (int64_t r = p + 1; r <= q_end; ++r) {
+        const float nb = (float)meta[2 * r].x;
+        const float4* s4 = reinterpret_cast<const float4*>(part + (size_t)(2 * r) * L + e);
+        const float4 a = s4[0], b = s4[1];
+        const float mb[4] = {a.x, a.z, b.x, b.z}, vb[4] = {a.y, a.w, b.y, b.w};
+        const float nn = na + nb;
+        const float wb = nb / nn, wab = na * nb / nn;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xFFFFFFFFu, nrm, off);
+        for (int u = 0; u < 4; ++u) {
+          const float dl = mb[u] - mean[u];
+          // mean += dl * nb / n and M2 += M2_b + dl^2 na nb / n, compensated
+          const float ym = __fsub_rn(__fmul_rn(dl, wb), mc[u]);
+          const float tm = __fadd_rn(mean[u], ym);
+          mc[u] = __fsub_rn(__fsub_rn(tm, mean[u]), ym);
+          mean[u] = tm;
+          const float yv = __fsub_rn(__fadd_rn(vb[u], __fmul_rn(__fmul_rn(dl, dl), wab)), vc[u]);
+          const float tv = __fadd_rn(m2[u], yv);
+          vc[u] = __fsub_rn(__fsub_rn(tv, m2[u]), yv);
+          m2[u] = tv;
+        }
+        na = nn;
+      }
+      nrm += nig_apply4<BF16>(mv, rbase, e, fresh, fm, fbw, mean, m2);
+    }
+    nrm = warp_sum(nrm);
     if (lane == 0) {
       mv.tsdf[row] = make_float2(sw.x + sd, Wn);
       mv.mnorm2[row] = nrm;
@@ -292,7 +465,9 @@ slim_status open_alloc_scratch(slim_map* m, OpenScratch& o, int64_t max_points) 
   if ((s = m->alloc(&o.vals_tmp, (size_t)cap)) != SLIM_OK) return s;
   if ((s = m->alloc(&o.pair_d, (size_t)cap)) != SLIM_OK) return s;
   if ((s = m->alloc(&o.pair_pt, (size_t)cap)) != SLIM_OK) return s;
-  if ((s = m->alloc(&o.seg_start, (size_t)cap)) != SLIM_OK) return s;
+  const int64_t pieces = (cap + kPiece - 1) / kPiece;
+  if ((s = m->alloc(&o.part, (size_t)pieces * 2 * (size_t)m->L)) != SLIM_OK) return s;
+  if ((s = m->alloc(&o.meta, (size_t)pieces * 2)) != SLIM_OK) return s;
   if ((s = m->alloc(&o.ctr, (size_t)kOpCounters)) != SLIM_OK) return s;
   unsigned char* tmp = nullptr;
   if ((s = m->alloc(&tmp, radix_sort_temp_bytes(cap))) != SLIM_OK) return s;
@@ -319,21 +494,26 @@ slim_status open_integrate(slim_map* m, const MapView& mv, OpenScratch& o, const
   k_open_pairs<<<grid, 256, 0, st>>>(mv, g, pts, n, o.keys, o.vals, o.pair_d, o.pair_pt, o.ctr,
                                      (uint32_t)o.pair_cap);
   const int64_t n_max = std::min<int64_t>(o.pair_cap, n * (int64_t)g.cap);
-  const int bits = 9 + ceil_log2((uint64_t)mv.block_cap);
+  // keys of pairs without a block (0xFFFFFFFF) must sort after every valid
+  // key within the sorted bits: valid keys stay below (block_cap + 1) << 9
+  const int bits = 9 + ceil_log2((uint64_t)mv.block_cap + 1);
   e = radix_sort_u32_devn(o.keys, o.vals, o.keys_tmp, o.vals_tmp, o.tmp, n_max, o.ctr + kOpPairs,
                           bits, st);
   if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
-  const unsigned hgrid = (unsigned)std::min<int64_t>((n_max + 255) / 256, 152 * 16);
-  k_open_heads<<<hgrid, 256, 0, st>>>(o.keys, o.ctr, o.seg_start, n_max);
   prof_end(m, tok, st);
   tok = prof_begin(m, SLIM_KERNEL_OPEN_APPLY, st);
-  const unsigned agrid = 152 * 8;
-  if (bf16)
-    k_open_apply<1><<<agrid, 256, 0, st>>>(mv, o.keys, o.vals, o.pair_d, o.pair_pt, o.seg_start,
-                                           o.ctr, sem, L, n_max);
-  else
-    k_open_apply<0><<<agrid, 256, 0, st>>>(mv, o.keys, o.vals, o.pair_d, o.pair_pt, o.seg_start,
-                                           o.ctr, sem, L, n_max);
+  const int64_t pieces = (n_max + kPiece - 1) / kPiece;
+  const unsigned fgrid = (unsigned)((pieces + 7) / 8);
+  const unsigned mgrid = 152 * 8;
+  if (bf16) {
+    k_open_frag<1><<<fgrid, 256, 0, st>>>(mv, o.keys, o.vals, o.pair_d, o.pair_pt, o.ctr, sem, L,
+                                          n_max, o.part, o.meta);
+    k_open_merge<1><<<mgrid, 256, 0, st>>>(mv, o.ctr, L, n_max, o.part, o.meta);
+  } else {
+    k_open_frag<0><<<fgrid, 256, 0, st>>>(mv, o.keys, o.vals, o.pair_d, o.pair_pt, o.ctr, sem, L,
+                                          n_max, o.part, o.meta);
+    k_open_merge<0><<<mgrid, 256, 0, st>>>(mv, o.ctr, L, n_max, o.part, o.meta);
+  }
   prof_end(m, tok, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));

@@ -61,7 +61,8 @@ EXPORTS = ["slim_map_params_default", "slim_map_create", "slim_map_destroy", "sl
            "slim_extract_tsdf", "slim_query", "slim_backward", "slim_integrate_batch",
            "slim_profile_enable", "slim_profile_read", "slim_autotune", "slim_query_rows_static",
            "slim_last_error"]
-KERNELS = ["traverse", "fuse_closed", "open_pairs", "open_apply", "query", "backward", "batch"]
+KERNELS = ["traverse", "fuse_closed", "open_pairs", "open_apply", "query", "backward", "batch",
+           "reset"]
 
 _lock = threading.Lock()
 _lib = None

@@ -90,3 +90,15 @@ def test_open_voxel_capacity_fault():
     with pytest.raises(slim.SlimError) as e:
         gpu_map(w, voxel_capacity=10)
     assert e.value.status == 3
+
+
+def test_open_long_runs_split_across_pieces():
+    """Full-resolution depth frames where single voxels collect thousands of
+    pixel observations in one frame (the camera close to a wall): runs far
+    longer than one piece of sorted pairs are cut and merged, and must give
+    the same batch update as the oracle's sequential one."""
+    w = synth.indoor_rgbd(seed=3, n_frames=200, width=640, height=480, dim=64,
+                          frames=[100, 0, 50])
+    g = to_np(gpu_map(w, voxel_capacity=400000).extract())
+    o = oracle_map(w).extract()
+    _compare(g, o)
