@@ -46,10 +46,20 @@ struct HashTile {
   static constexpr size_t kSmem = (size_t)kTbl * 14 + (size_t)kVc * 8 + 16 * 4;
 };
 
+// Bucket of a block key in the tile's block table (a cheap 32-bit mix: the
+// table holds a few dozen keys per tile).
+__device__ __forceinline__ uint32_t tile_hash(uint64_t kb) {
+  uint32_t h = ((uint32_t)kb * 0x9E3779B1u) ^ ((uint32_t)(kb >> 32) * 0x85EBCA77u);
+  return h ^ (h >> 15);
+}
+
+// Insert-or-find a block key; the thread that inserts it appends the entry
+// to the tile's block list. Returns the entry, or 0xFFFFFFFF when full.
 template <int TP>
-__device__ __forceinline__ uint32_t htbl_insert(uint64_t* tb, uint64_t kb) {
+__device__ __forceinline__ uint32_t htbl_insert(uint64_t* tb, uint64_t kb, uint16_t* blist,
+                                                uint32_t* nblk) {
   constexpr int N = HashTile<TP>::kTbl;
-  uint32_t h = (uint32_t)mix64(kb) & (N - 1);
+  uint32_t h = tile_hash(kb) & (N - 1);
   for (int it = 0; it < N; ++it) {
     const uint64_t cur = *(volatile uint64_t*)&tb[h];
     if (cur == kb) return h;
@@ -57,7 +67,11 @@ __device__ __forceinline__ uint32_t htbl_insert(uint64_t* tb, uint64_t kb) {
       const unsigned long long prev = atomicCAS((unsigned long long*)&tb[h],
                                                 (unsigned long long)kEmptyKey,
                                                 (unsigned long long)kb);
-      if (prev == kEmptyKey || prev == kb) return h;
+      if (prev == kEmptyKey) {
+        blist[atomicAdd(nblk, 1u)] = (uint16_t)h;
+        return h;
+      }
+      if (prev == kb) return h;
     }
     h = (h + 1) & (N - 1);
   }
@@ -67,7 +81,7 @@ __device__ __forceinline__ uint32_t htbl_insert(uint64_t* tb, uint64_t kb) {
 template <int TP>
 __device__ __forceinline__ uint32_t htbl_find(const uint64_t* tb, uint64_t kb) {
   constexpr int N = HashTile<TP>::kTbl;
-  uint32_t h = (uint32_t)mix64(kb) & (N - 1);
+  uint32_t h = tile_hash(kb) & (N - 1);
   for (int it = 0; it < N; ++it) {
     const uint64_t cur = tb[h];
     if (cur == kb) return h;
@@ -156,11 +170,34 @@ __device__ __forceinline__ uint32_t argmax_row(const float* __restrict__ row, in
 }
 
 // One tile: points [tile * tile_points, (tile + 1) * tile_points) of a scan.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ int job_of(const HashBatch& b, uint32_t t) {
+  int jb = 0;
+  while (jb + 1 < b.n_jobs && t >= b.job[jb + 1].tile_begin) ++jb;
+  return jb;
+}
+
+// Ask L2 for this thread's point and probability row of tile t (the tile the
+// CTA takes next), so that its loads at the start of that tile hit L2.
+__device__ __forceinline__ void prefetch_tile(const HashBatch& b, uint32_t t) {
+  const HashJob& J = b.job[job_of(b, t)];
+  const int64_t j = (int64_t)(t - J.tile_begin) * J.tile_points + threadIdx.x;
+  if ((int)threadIdx.x >= J.tile_points || j >= J.n) return;
+  prefetch_l2(J.pts + 3 * j);
+  const float* row = J.sem + (size_t)j * J.K;
+  prefetch_l2(row);
+  prefetch_l2(row + J.K - 1);
+}
+
 template <int TP>
 __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom& g,
                                                const float* __restrict__ pts,
                                                const float* __restrict__ sem, int64_t n, int K,
-                                               int tile_points, int64_t tile, unsigned char* sm) {
+                                               int tile_points, int64_t tile, unsigned char* sm,
+                                               const HashBatch& b, const uint32_t* s_next) {
   using H = HashTile<TP>;
   uint64_t* tb_key = reinterpret_cast<uint64_t*>(sm);
   unsigned long long* vc = reinterpret_cast<unsigned long long*>(tb_key + H::kTbl);
@@ -191,6 +228,7 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
     reinterpret_cast<ulonglong2*>(vc)[e] = make_ulonglong2(kVcEmpty, kVcEmpty);
   __syncthreads();
   if (misc[0]) return;
+  if (s_next && *s_next < b.total_tiles) prefetch_tile(b, *s_next);
 
   // 1. band DDA, aggregating every pair into the (voxel, class) table
   const float qscale = __fdiv_rn(1048576.0f, g.tau);
@@ -199,14 +237,11 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
   const bool valid = mine && ray_setup(g, p0, p1, p2, ry);
   if (valid) {
     Ray r2 = ry;
-    uint64_t last = kEmptyKey;
     uint32_t last_tb = 0;
     int k = 0;
-    ray_for_each(g, r2, [&](int32_t i0, int32_t i1, int32_t i2, float d) {
-      const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
-      if (kb != last) {
-        last = kb;
-        last_tb = htbl_insert<TP>(tb_key, kb);
+    ray_for_each_blk(g, r2, [&](int32_t i0, int32_t i1, int32_t i2, float d, bool new_block) {
+      if (new_block) {
+        last_tb = htbl_insert<TP>(tb_key, pack_block(i0 >> 3, i1 >> 3, i2 >> 3), blist, &misc[3]);
         if (last_tb == 0xFFFFFFFFu) misc[2] = 1;
       }
       const int idx = k++;
@@ -222,18 +257,6 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
     if (tid == 0) raise_status(mv.ctr, kDevInternal, 4);
     return;
   }
-  // compact the occupied block-table entries
-#pragma unroll
-  for (int q = 0; q < H::kTbl / TP; ++q) {
-    const int e = tid + q * TP;
-    const bool occ = tb_key[e] != kEmptyKey;
-    const unsigned b = __ballot_sync(0xFFFFFFFFu, occ);
-    uint32_t base = 0;
-    if (lane_id() == 0 && b) base = atomicAdd(&misc[3], (uint32_t)__popc(b));
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (occ) blist[base + __popc(b & ((1u << lane_id()) - 1u))] = (uint16_t)e;
-  }
-  __syncthreads();
   const int nblk = (int)misc[3];
 
   // 2. insert-or-find each distinct block (compacted items tid + TP q); a
@@ -309,17 +332,9 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
   for (int e = tid; e < H::kVc; e += TP) {
     const unsigned long long w = vc[e];
     if (w == kVcEmpty) continue;
-    const uint32_t key = (uint32_t)(w >> kVcKeyShift);
-    if ((key >> 15) >= (uint32_t)H::kTbl) {  // consistency check, never expected
-      raise_status(mv.ctr, kDevInternal, 6);
-      continue;
-    }
+    const uint32_t key = (uint32_t)(w >> kVcKeyShift);  // entry < kTbl, class < K by construction
     const uint32_t slot = tb_slot[key >> 15];
-    if (slot >= kFailSlot) continue;
-    if (slot >= mv.block_cap || (key & 63u) >= (uint32_t)mv.K) {
-      raise_status(mv.ctr, kDevInternal, 7);
-      continue;
-    }
+    if (slot >= mv.block_cap) continue;  // kFailSlot: a fault was raised for the block
     const uint32_t cnt = (uint32_t)(w >> kVcCntShift) & 511u;
     const int32_t qs = (int32_t)(uint32_t)(w & ((1ull << kVcCntShift) - 1ull)) -
                        (int32_t)(cnt * kQOne);
@@ -351,25 +366,35 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
 }
 
 // Persistent form: a grid sized to the resident capacity takes tiles from a
-// shared counter until every tile of every job (a scan of some map) is done;
-// the last CTA to finish resets the counter for the next launch. Tiles of
+// shared counter until every tile of every job (a scan of some map) is done
+// (while tiles remain for another round, each CTA holds one reserved tile
+// ahead, whose inputs it prefetches); the last CTA to finish resets the
+// counter for the next launch. Tiles of
 // different jobs (scans of the same or of different maps) run concurrently:
 // the per-scan updates are additions (Theorem 1), so their order is free.
 template <int TP>
 __global__ void __launch_bounds__(TP, 1024 / TP) k_fuse_hash_persistent(const __grid_constant__ HashBatch b) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ uint32_t s_t;
-  for (;;) {
-    if (threadIdx.x == 0) s_t = atomicAdd(&b.work[0], 1u);
-    __syncthreads();
-    const uint32_t t = s_t;
-    __syncthreads();
-    if (t >= b.total_tiles) break;
-    int jb = 0;
-    while (jb + 1 < b.n_jobs && t >= b.job[jb + 1].tile_begin) ++jb;
-    const HashJob& J = b.job[jb];
+  if (threadIdx.x == 0) s_t = atomicAdd(&b.work[0], 1u);
+  __syncthreads();
+  uint32_t t = s_t;
+  __syncthreads();
+  while (t < b.total_tiles) {
+    // while at least another full round of tiles remains, reserve the next
+    // tile now (the tile prefetches its inputs into L2); near the end take
+    // it only when this one is done, so that no CTA holds work others wait for
+    const bool ahead = t + gridDim.x < b.total_tiles;
+    if (ahead && threadIdx.x == 0) s_t = atomicAdd(&b.work[0], 1u);
+    const HashJob& J = b.job[job_of(b, t)];
     fuse_hash_tile<TP>(J.mv, J.g, J.pts, J.sem, J.n, J.K, J.tile_points, (int64_t)(t - J.tile_begin),
-                       sm);
+                       sm, b, ahead ? &s_t : nullptr);
+    __syncthreads();
+    if (!ahead) {
+      if (threadIdx.x == 0) s_t = atomicAdd(&b.work[0], 1u);
+      __syncthreads();
+    }
+    t = s_t;
     __syncthreads();
   }
   if (threadIdx.x == 0) {

@@ -111,6 +111,50 @@ __device__ __forceinline__ bool ray_step(Ray& ry) {
   return true;
 }
 
+// ray_step that also reports whether the voxel entered lies in another 8^3
+// block than the one left (the stepped index crossed a multiple of 8).
+__device__ __forceinline__ bool ray_step_blk(Ray& ry, bool& crossed) {
+  int a = 0;
+  float m = ry.m0;
+  if (ry.m1 < m) { a = 1; m = ry.m1; }
+  if (ry.m2 < m) { a = 2; m = ry.m2; }
+  if (m > ry.t1) return false;
+  int32_t o, nw;
+  if (a == 0) {
+    o = ry.i0;
+    nw = ry.i0 += ry.s0;
+    ry.m0 = __fadd_rn(ry.m0, ry.e0);
+  } else if (a == 1) {
+    o = ry.i1;
+    nw = ry.i1 += ry.s1;
+    ry.m1 = __fadd_rn(ry.m1, ry.e1);
+  } else {
+    o = ry.i2;
+    nw = ry.i2 += ry.s2;
+    ry.m2 = __fadd_rn(ry.m2, ry.e2);
+  }
+  crossed = ((o ^ nw) >> 3) != 0;
+  return true;
+}
+
+// As ray_for_each, with f(i0, i1, i2, d, new_block): new_block is true for
+// the first kept visit and for every kept visit whose block differs from
+// the previous kept visit's (a block change at a skipped visit carries over).
+template <class F>
+__device__ __forceinline__ void ray_for_each_blk(const ScanGeom& g, Ray& ry, F&& f) {
+  bool fresh = true;
+  for (int k = 0; k < g.cap; ++k) {
+    float d = ray_sdf(ry, g.v);
+    if (!(d < -g.tau)) {
+      f(ry.i0, ry.i1, ry.i2, d > g.tau ? g.tau : d, fresh);
+      fresh = false;
+    }
+    bool crossed;
+    if (!ray_step_blk(ry, crossed)) break;
+    fresh |= crossed;
+  }
+}
+
 // Visit every kept (voxel, point) observation of one point's band in ray
 // order: f(i0, i1, i2, d) with d clamped to tau; visits with d < -tau are
 // skipped. At most g.cap voxels are entered.
