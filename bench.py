@@ -553,13 +553,31 @@ def run_indoor(args):
                                                "peak_source": kind},
                                   "hbm_gbs": rows * (2 * 512 + 8) / (kq / 1e3) / 1e9}}
         m.close()
+    # the query kernel at a size where it is a real contraction: 2^20 BF16
+    # rows of l = 512 against 256 queries, caller-held rows
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    nrow = 1 << 20
+    rows = torch.randn(nrow, 512, device="cuda", generator=gen).to(torch.bfloat16)
+    qb = torch.from_numpy(synth.random_queries(7, 256, 512)).to(torch.bfloat16).cuda()
+    lab = torch.empty(nrow, dtype=torch.int32, device="cuda")
+    prb = torch.empty(nrow, dtype=torch.float32, device="cuda")
+    sms = _timed(lambda: slim.slim_query_rows_static(rows, qb, 0.01, 0.1, lab, prb),
+                 args.steps, args.warmup, stream)
+    peak, kind = _bf16_peak()
+    flops = 2.0 * nrow * 512 * 256
+    big = {"rows": nrow, "l": 512, "queries": 256, "ms": sms,
+           "tflops": flops / (sms / 1e3) / 1e12,
+           "tensor_frac": flops / (sms / 1e3) / 1e12 / peak, "tensor_peak": peak,
+           "hbm_gbs": nrow * 512 * 2 / (sms / 1e3) / 1e9,
+           "hbm_frac": nrow * 512 * 2 / (sms / 1e3) / 1e9 / measured_peak()[0],
+           "peak_source": kind, "call": "slim_query_rows_static (row norms + tcgen05 GEMM + epilogue)"}
     line = {"metric": "open-set points integrated/s (NIG, l=512) and query TFLOP/s",
             "value": out["bf16"]["points_per_s"], "unit": "points/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "dtype": "f32 accumulate, bf16 storage", "data": "synthetic",
             "config": {"workload": f"indoor-rgbd {args.frames} frames 640x480, l=512, voxel "
                                    "0.05 m, trunc 0.15 m, 256 queries T=0.01"},
-            "storage": out}
+            "storage": out, "query_1M_rows": big}
     print(json.dumps(line), flush=True)
     return 0
 

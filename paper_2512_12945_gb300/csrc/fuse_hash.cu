@@ -5,10 +5,11 @@
 //   1. every thread loads its point and class probabilities first (the
 //      probability row as independent float4 loads, argmax afterwards), then
 //      marches the band; each kept pair is added at once into a tile-local
-//      table keyed by (tile block entry, local voxel, class). One 64-bit word
-//      per entry holds the key, the count and the sum of the pair's SDF in
-//      fixed point (units of tau / 2^20), so a pair costs one shared load and
-//      one shared atomic; no pair list is staged and nothing is sorted;
+//      table keyed by (tile block entry, local voxel, class): an entry is a
+//      32-bit key word and a 32-bit count side by side, plus a 32-bit sum of
+//      the pair's SDF in fixed point (units of tau / 2^20); a pair costs one
+//      shared load and two 32-bit shared atomic adds (plus a compare-and-swap
+//      when it claims the entry); no pair list is staged, nothing is sorted;
 //   2. each distinct block of the tile (compacted first) is inserted into
 //      (or found in) the map's hash by its own thread; a block this thread
 //      creates is published at once (its records are already zero: the pool
@@ -31,19 +32,17 @@
 
 namespace slim {
 
-constexpr unsigned long long kVcEmpty = ~0ull;
-constexpr int kVcKeyShift = 39;    // key: tile block entry << 15 | local << 6 | class
-constexpr int kVcCntShift = 30;    // count: 9 bits (at most TP <= 256 pairs per entry)
-constexpr uint32_t kQOne = 1u << 20;  // fixed-point unit of the SDF sum is tau / 2^20
+constexpr uint32_t kVcEmpty = 0xFFFFFFFFu;  // key: tile block entry << 15 | local << 6 | class
+constexpr uint32_t kQOne = 1u << 20;        // fixed-point unit of the SDF sum is tau / 2^20
 
 template <int TP>
 struct HashTile {
   static constexpr int kTbl = 4 * TP;    // block table entries (>= distinct blocks of a tile)
   static constexpr int kVc = 8 * TP;     // (voxel, class) accumulators
   static constexpr int kVcBits = kVc == 2048 ? 11 : (kVc == 1024 ? 10 : 9);
-  // tb_key u64 + tb_slot u32 + compacted list u16 per block entry, one
-  // u64 per accumulator, counters
-  static constexpr size_t kSmem = (size_t)kTbl * 14 + (size_t)kVc * 8 + 16 * 4;
+  // tb_key u64 + tb_slot u32 + block list u16 per block entry; per
+  // accumulator a (key, count) u32 pair and a u32 sum; counters
+  static constexpr size_t kSmem = (size_t)kTbl * 14 + (size_t)kVc * 12 + 16 * 4;
 };
 
 // Bucket of a block key in the tile's block table (a cheap 32-bit mix: the
@@ -91,22 +90,23 @@ __device__ __forceinline__ uint32_t htbl_find(const uint64_t* tb, uint64_t kb) {
   return 0xFFFFFFFFu;
 }
 
-// Add one pair (key, q) to the (voxel, class) table: claim an empty word
-// with the first observation, else add (1 count, q) to the word holding the
-// key. Returns false when the probe runs out.
+// Add one pair (key, q) to the (voxel, class) table: vkc[2e] is the entry's
+// key (claimed by compare-and-swap), vkc[2e + 1] its count, vsum[e] its
+// fixed-point SDF sum (q = rint(d 2^20 / tau) + 2^20, at most TP pairs per
+// entry: below 2^30). Returns false when the probe runs out.
 template <int TP>
-__device__ __forceinline__ bool vc_add(unsigned long long* tbl, uint32_t key, uint32_t q) {
+__device__ __forceinline__ bool vc_add(uint32_t* vkc, uint32_t* vsum, uint32_t key, uint32_t q) {
   constexpr int N = HashTile<TP>::kVc;
-  const unsigned long long inc = (1ull << kVcCntShift) | (unsigned long long)q;
   uint32_t h = (key * 2654435761u) >> (32 - HashTile<TP>::kVcBits);
   for (int it = 0; it < 64; ++it) {
-    unsigned long long cur = *(volatile unsigned long long*)&tbl[h];
+    uint32_t cur = *(volatile uint32_t*)&vkc[2 * h];
     if (cur == kVcEmpty) {
-      cur = atomicCAS(&tbl[h], kVcEmpty, ((unsigned long long)key << kVcKeyShift) | inc);
-      if (cur == kVcEmpty) return true;
+      cur = atomicCAS(&vkc[2 * h], kVcEmpty, key);
+      if (cur == kVcEmpty) cur = key;
     }
-    if ((uint32_t)(cur >> kVcKeyShift) == key) {
-      atomicAdd(&tbl[h], inc);
+    if (cur == key) {
+      atomicAdd(&vkc[2 * h + 1], 1u);
+      atomicAdd(&vsum[h], q);
       return true;
     }
     h = (h + 1) & (N - 1);
@@ -200,8 +200,9 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
                                                const HashBatch& b, const uint32_t* s_next) {
   using H = HashTile<TP>;
   uint64_t* tb_key = reinterpret_cast<uint64_t*>(sm);
-  unsigned long long* vc = reinterpret_cast<unsigned long long*>(tb_key + H::kTbl);
-  uint32_t* tb_slot = reinterpret_cast<uint32_t*>(vc + H::kVc);
+  uint32_t* vkc = reinterpret_cast<uint32_t*>(tb_key + H::kTbl);  // (key, count) per entry
+  uint32_t* vsum = vkc + 2 * H::kVc;
+  uint32_t* tb_slot = vsum + H::kVc;
   uint16_t* blist = reinterpret_cast<uint16_t*>(tb_slot + H::kTbl);
   uint32_t* misc = reinterpret_cast<uint32_t*>(blist + H::kTbl);
 
@@ -225,7 +226,9 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
   for (int e = tid; e < H::kTbl / 2; e += TP)
     reinterpret_cast<ulonglong2*>(tb_key)[e] = make_ulonglong2(kEmptyKey, kEmptyKey);
   for (int e = tid; e < H::kVc / 2; e += TP)
-    reinterpret_cast<ulonglong2*>(vc)[e] = make_ulonglong2(kVcEmpty, kVcEmpty);
+    reinterpret_cast<uint4*>(vkc)[e] = make_uint4(kVcEmpty, 0u, kVcEmpty, 0u);
+  for (int e = tid; e < H::kVc / 4; e += TP)
+    reinterpret_cast<uint4*>(vsum)[e] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   if (misc[0]) return;
   if (s_next && *s_next < b.total_tiles) prefetch_tile(b, *s_next);
@@ -249,7 +252,7 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
       const uint32_t key = (last_tb << 15) | ((uint32_t)local_index(i0, i1, i2) << 6) | cls;
       int qi = __float2int_rn(__fmul_rn(d, qscale));
       qi = max(-(int)kQOne, min((int)kQOne, qi));
-      if (!vc_add<TP>(vc, key, (uint32_t)(qi + (int)kQOne))) ovf = idx;
+      if (!vc_add<TP>(vkc, vsum, key, (uint32_t)(qi + (int)kQOne))) ovf = idx;
     });
   }
   __syncthreads();
@@ -330,14 +333,13 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
   // 3. flush: one vector red.add (S_k, c_k) per entry
   const float qunit = __fmul_rn(g.tau, 1.0f / 1048576.0f);  // exact: a power-of-two scale
   for (int e = tid; e < H::kVc; e += TP) {
-    const unsigned long long w = vc[e];
-    if (w == kVcEmpty) continue;
-    const uint32_t key = (uint32_t)(w >> kVcKeyShift);  // entry < kTbl, class < K by construction
+    const uint2 kc = reinterpret_cast<const uint2*>(vkc)[e];
+    const uint32_t key = kc.x;  // entry < kTbl, class < K by construction
+    if (key == kVcEmpty) continue;
     const uint32_t slot = tb_slot[key >> 15];
     if (slot >= mv.block_cap) continue;  // kFailSlot: a fault was raised for the block
-    const uint32_t cnt = (uint32_t)(w >> kVcCntShift) & 511u;
-    const int32_t qs = (int32_t)(uint32_t)(w & ((1ull << kVcCntShift) - 1ull)) -
-                       (int32_t)(cnt * kQOne);
+    const uint32_t cnt = kc.y;
+    const int32_t qs = (int32_t)vsum[e] - (int32_t)(cnt * kQOne);
     float* r = mv.rec + ((size_t)slot * kBlockVoxels + ((key >> 6) & 511u)) * mv.rs;
     red_add_v2(r + 2 * (key & 63u), __fmul_rn((float)qs, qunit), (float)cnt);
   }
