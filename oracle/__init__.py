@@ -71,6 +71,8 @@ def _load():
             lib.ora_count.argtypes = [P]
             lib.ora_extract.restype = ctypes.c_int64
             lib.ora_extract.argtypes = [P, P, P, P, P, P, ctypes.c_int32]
+            lib.ora_uncertainty.restype = ctypes.c_int64
+            lib.ora_uncertainty.argtypes = [P, P]
             lib.ora_query.restype = None
             lib.ora_query.argtypes = [P, ctypes.c_int64, ctypes.c_int32, P, ctypes.c_int32,
                                       ctypes.c_double, ctypes.c_double, P, P, P]
@@ -156,6 +158,16 @@ class OracleMap:
         if beta is not None:
             out["beta"] = beta
         return out
+
+    def uncertainty(self):
+        """Closed set: (n, K+1) Dirichlet class-probability variances and the
+        posterior-predictive entropy; open set: (n, l) Student-t predictive
+        variances (+inf where W <= 2). Same voxel order as extract()."""
+        n = self.count()
+        w = self.w + 1 if self.params.mode != OPEN else self.w
+        unc = np.zeros((n, w))
+        self.lib.ora_uncertainty(self.h, _ptr(unc))
+        return unc
 
     def backward_scan(self, pts, pose, sem, gD, gS, gB=None):
         """Per-point dL/dsem (n,w) and dL/dxyz (n,3); call extract() first."""

@@ -472,6 +472,52 @@ int64_t ora_extract(void* h, int32_t* ijk, double* D, double* W, double* sem, do
   return (int64_t)m.order.size();
 }
 
+// Uncertainty read-out, in the order of ora_extract (the map is re-sorted
+// here). Closed set (Sec. III-C: the Dirichlet posterior Dir(alpha~) with
+// alpha~_i = alpha0 + c_i, A = sum_i alpha~_i): unc is n x (K + 1), first
+// the variance of each class probability, alpha~_i (A - alpha~_i) /
+// (A^2 (A + 1)), then the entropy -sum_i p_i ln p_i of the posterior
+// predictive p_i = alpha~_i / A (Eq. dir_to_cat; a zero p_i adds nothing).
+// Open set (Eq. student_t): the predictive of each element is a Student-t
+// with 2 nu degrees of freedom, location m and scale^2 beta (lambda + 1) /
+// (lambda nu); its variance 2 nu / (2 nu - 2) * scale^2 exists for 2 nu > 2.
+// With lambda = 2 nu = W (end of Sec. III-D) that is
+// 2 beta (W + 1) / (W (W - 2)); unc is n x l, +inf where W <= 2.
+int64_t ora_uncertainty(void* h, double* unc) {
+  Map& m = *(Map*)h;
+  const Params& P = m.p;
+  std::vector<VKey> order;
+  for (auto& kv : m.vox) order.push_back(kv.first);
+  std::sort(order.begin(), order.end(), key_less);
+  const int w = sem_width(P);
+  for (size_t j = 0; j < order.size(); ++j) {
+    const Rec& r = m.vox.at(order[j]);
+    if (P.mode != OPEN) {
+      double A = 0.0;
+      for (int c = 0; c < w; ++c) A += P.alpha0 + r.sem[c];
+      double H = 0.0;
+      for (int c = 0; c < w; ++c) {
+        const double a = P.alpha0 + r.sem[c];
+        unc[j * (w + 1) + c] = a * (A - a) / (A * A * (A + 1.0));
+        const double p = a / A;
+        if (p > 0.0) H -= p * std::log(p);
+      }
+      unc[j * (w + 1) + w] = H;
+    } else {
+      const double lam = r.W, nu = r.W / 2.0;
+      for (int c = 0; c < w; ++c) {
+        if (!(2.0 * nu > 2.0)) {
+          unc[j * w + c] = INFINITY;
+          continue;
+        }
+        const double scale2 = r.beta[c] * (lam + 1.0) / (lam * nu);
+        unc[j * w + c] = 2.0 * nu / (2.0 * nu - 2.0) * scale2;
+      }
+    }
+  }
+  return (int64_t)order.size();
+}
+
 // Open-set read-out (end of Sec. III-D, Fig. "sit"): cosine similarity of each
 // voxel mean m (rows, n x l, FP64) against Q query embeddings (Q x l), softmax
 // over the queries of cos / temperature, most probable query, kept when its

@@ -506,3 +506,46 @@ def test_dda_tie_breaks_to_lowest_axis():
         assert (np.abs(steps).sum(axis=1) == 1).all()
         assert len(axes) >= 4
         assert axes == [0, 1, 2] * (len(axes) // 3) + [0, 1, 2][:len(axes) % 3]
+
+
+def test_uncertainty_closed_matches_scipy_dirichlet():
+    """Closed-set uncertainty read-out: per-class variance of the Dirichlet
+    posterior and entropy of its predictive, against scipy's Dirichlet and
+    entropy routines (soft counts, alpha0 = 0.5)."""
+    st = pytest.importorskip("scipy.stats")
+    w = synth.room_lidar(seed=1, n_scans=2, K=10, mode="soft")
+    m = oracle.OracleMap(voxel_size=w.voxel_size, trunc=w.trunc, mode=oracle.CLOSED_SOFT,
+                         num_classes=10, min_range=w.min_range, max_range=w.max_range,
+                         alpha0=0.5)
+    for s in w.scans:
+        m.integrate(s["pts"], s["pose"], s["sem"])
+    ext = m.extract()
+    unc = m.uncertainty()
+    assert unc.shape == (len(ext["W"]), 11)
+    rng = np.random.default_rng(0)
+    for j in rng.choice(len(ext["W"]), 50, replace=False):
+        alpha = 0.5 + ext["sem"][j]
+        np.testing.assert_allclose(unc[j, :10], st.dirichlet(alpha).var(), rtol=1e-12)
+        np.testing.assert_allclose(unc[j, 10], st.entropy(alpha / alpha.sum()), rtol=1e-12)
+
+
+def test_uncertainty_open_matches_scipy_student_t():
+    """Open-set uncertainty read-out: the variance of the Student-t predictive
+    t_{2 nu}(m, beta (lambda + 1) / (lambda nu)) with lambda = 2 nu = W,
+    against scipy's t distribution; infinite where 2 nu <= 2."""
+    st = pytest.importorskip("scipy.stats")
+    w = synth.indoor_rgbd(seed=3, n_frames=40, width=48, height=36, dim=16, frames=[0, 1])
+    m = oracle.OracleMap(voxel_size=w.voxel_size, trunc=w.trunc, mode=oracle.OPEN, embed_dim=16,
+                         min_range=w.min_range, max_range=w.max_range)
+    for s in w.scans:
+        m.integrate(s["pts"], s["pose"], s["sem"])
+    ext = m.extract()
+    unc = m.uncertainty()
+    W = ext["W"]
+    assert (W <= 2).any() and (W > 2).any()
+    assert np.all(np.isinf(unc[W <= 2]))
+    for j in np.flatnonzero(W > 2)[:40]:
+        lam, nu = W[j], W[j] / 2.0
+        scale = np.sqrt(ext["beta"][j] * (lam + 1.0) / (lam * nu))
+        ref = st.t(df=2.0 * nu, loc=ext["sem"][j], scale=scale).var()
+        np.testing.assert_allclose(unc[j], ref, rtol=1e-12)
