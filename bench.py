@@ -161,20 +161,36 @@ def algorithmic_bytes(counts, n_scans):
     return out
 
 
-def kernel_source_sha():
-    """Hash of the sources of the dominant kernel (k_fuse_hash_persistent)."""
+STRATEGY = {0: ("k_fuse_direct", "fuse_direct.cu",
+                 "slim_integrate_batch: 16 scans per grid, direct per-pair red.add into "
+                 "L2-resident records")}
+HASH_STRATEGY = ("k_fuse_hash_persistent", "fuse_hash.cu",
+                 "slim_integrate_batch: 16 scans per persistent launch, shared-memory "
+                 "(voxel, class) hash tiles of {} points")
+
+
+def strategy(tile):
+    """(dominant kernel, its source file, path description) for the autotuned
+    strategy (0 = direct reductions, else hash tiles of that many points)."""
+    if tile == 0:
+        return STRATEGY[0]
+    return HASH_STRATEGY[0], HASH_STRATEGY[1], HASH_STRATEGY[2].format(tile)
+
+
+def kernel_source_sha(src="fuse_direct.cu"):
+    """Hash of the sources of the dominant kernel."""
     h = hashlib.sha256()
-    for f in ("fuse_hash.cu", "common.cuh", "geometry.cuh", "hash.cuh"):
+    for f in (src, "closed_common.cuh", "common.cuh", "geometry.cuh", "hash.cuh"):
         with open(os.path.join(ROOT, "paper_2512_12945_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def stored_traffic():
+def stored_traffic(kernel, src):
     try:
         with open(TRAFFIC) as f:
-            t = json.load(f)
-        if t.get("source_sha") == kernel_source_sha():
+            t = json.load(f).get(kernel, {})
+        if t.get("source_sha") == kernel_source_sha(src):
             return t.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -259,6 +275,7 @@ def run_ours(args):
     pts = [torch.from_numpy(s["pts"]).cuda() for s in w.scans]
     sem = [torch.from_numpy(s["sem"]).cuda() for s in w.scans]
     tile = m.autotune(pts[len(pts) // 2], w.scans[len(pts) // 2]["pose"], sem[len(pts) // 2])
+    kname, ksrc, kpath = strategy(tile)
     poses = [np.ascontiguousarray(np.asarray(s["pose"], np.float64).reshape(16)) for s in w.scans]
     args_c = [(ctypes.c_void_p(p.data_ptr()), p.shape[0], po.ctypes.data_as(ctypes.c_void_p),
                ctypes.c_void_p(se.data_ptr())) for p, se, po in zip(pts, sem, poses)]
@@ -340,9 +357,10 @@ def run_ours(args):
                                  for s in w.scans))
     value = ws * valid_per_step * args.steps / (ms_max / 1e3)
 
-    # roofline of the dominant kernel (the persistent batched integration
-    # kernel): algorithmic bytes of the scans one launch integrates / its
-    # CUDA-event time, averaged over the launches of the timed region
+    # roofline of the dominant kernel (the batched integration kernel of the
+    # autotuned strategy): algorithmic bytes of the scans one launch
+    # integrates / its CUDA-event time, averaged over the launches of the
+    # timed region
     roof = None
     peak, peak_kind = measured_peak()
     if counts is not None and "batch" in prof:
@@ -352,8 +370,8 @@ def run_ours(args):
         avg_ms = kms / nl
         achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": stored_traffic(),
-                "kernel": "k_fuse_hash_persistent", "peak_source": peak_kind,
+                "frac": round(achieved / peak, 4), "traffic": stored_traffic(kname, ksrc),
+                "kernel": kname, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": int(bytes_per_launch),
                 "scans_per_launch": round(args.scans * args.steps / nl, 2),
                 "avg_launch_ms": round(avg_ms, 5),
@@ -425,18 +443,36 @@ def run_ours(args):
     torch.cuda.synchronize()
     pms = p0.elapsed_time(p1) / npl
     variants["plain"] = {"value": valid_per_step / (pms / 1e3), "ms_per_step": pms, "steps": npl,
-                         "path": "slim_integrate per scan, hash aggregation"}
-    for agg in ("sort",):
+                         "path": "slim_integrate per scan, " + ("direct reductions" if tile == 0
+                                                                else f"hash tiles of {tile}")}
+    # the other strategies, each on its own map: the sort aggregation and
+    # both closed one-hot strategies per scan and batched
+    paths = {"sort": ("sort", 0, "slim_integrate per scan, CTA radix sort + segmented reduction"),
+             "direct": ("direct", 0, "slim_integrate per scan, direct per-pair red.add"),
+             "direct_batch": ("direct", 0, "slim_integrate_batch, 16 scans per grid, direct "
+                                           "per-pair red.add"),
+             "hash": ("hash", 256, "slim_integrate per scan, shared-memory hash tiles of 256"),
+             "hash_batch": ("hash", 256, "slim_integrate_batch, 16 scans per persistent launch, "
+                                         "shared-memory hash tiles of 256")}
+    for var in ("sort", "direct", "direct_batch", "hash", "hash_batch"):
+        agg, tp, _ = paths[var]
         mv = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=w.num_classes,
                       min_range=w.min_range, max_range=w.max_range,
                       body_from_sensor=w.body_from_sensor, block_capacity=args.block_capacity,
-                      hash_capacity=1 << 21, max_points=131072, aggregation=agg)
+                      hash_capacity=1 << 21, max_points=131072, aggregation=agg, tile_points=tp)
         hv = mv.handle
+        vitems = (slim.slim_batch_item * len(args_c))()
+        for k in range(len(args_c)):
+            vitems[k] = items[k]
+            vitems[k].map = hv
 
         def step_v():
             L.slim_map_reset(hv, sp)
-            for a in args_c:
-                L.slim_integrate(hv, a[0], a[1], a[2], a[3], sp)
+            if var.endswith("_batch"):
+                L.slim_integrate_batch(vitems, len(args_c), sp)
+            else:
+                for a in args_c:
+                    L.slim_integrate(hv, a[0], a[1], a[2], a[3], sp)
 
         for _ in range(2):
             step_v()
@@ -451,8 +487,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         mv.sync()
         vms = a0.elapsed_time(a1) / nv
-        variants[agg] = {"value": valid_per_step / (vms / 1e3), "ms_per_step": vms, "steps": nv,
-                         "path": "slim_integrate per scan, CTA radix sort + segmented reduction"}
+        variants[var] = {"value": valid_per_step / (vms / 1e3), "ms_per_step": vms, "steps": nv,
+                         "path": paths[var][2]}
         mv.close()
 
     launches = sum(v[0] for v in prof.values())
@@ -462,8 +498,7 @@ def run_ours(args):
             "config": workload_config(args.scans), "roofline": roof, "cpu_baseline": cpu,
             "e2e": e2e, "clocks": clocks.summary(), "gpu_launches": launches,
             "kernels_ms": {k: round(v[1], 3) for k, v in prof.items()},
-            "path": "slim_integrate_batch: 16 scans per persistent launch, shared-memory "
-                    "(voxel, class) hash aggregation", "tile_points": tile,
+            "path": kpath, "tile_points": tile,
             "variants": variants,
             "map": {"blocks": stats["blocks"],
                     "oracle_voxels": counts["meta"]["total_voxels"] if counts else None}}

@@ -64,15 +64,24 @@ typedef enum {
 
 typedef enum { SLIM_STORE_F32 = 0, SLIM_STORE_BF16 = 1 } slim_storage;
 
-/* How a closed-set tile groups its (voxel, point) pairs before the one
- * global update per voxel (both give the same result; Theorem 1 makes the
- * grouping free):
- *   SLIM_AGG_SORT  stable CTA radix sort of the pairs by voxel key, then a
- *                  warp segmented reduction over each voxel's run;
- *   SLIM_AGG_HASH  one-hot only: each pair is added at once into a
- *                  shared-memory table keyed by (voxel, class);
- *   SLIM_AGG_AUTO  hash for one-hot, sort for soft counts. */
-typedef enum { SLIM_AGG_AUTO = 0, SLIM_AGG_SORT = 1, SLIM_AGG_HASH = 2 } slim_aggregation;
+/* How closed-set (voxel, point) pairs reach the records (all give the same
+ * result up to FP32 summation order; Theorem 1 makes the grouping free):
+ *   SLIM_AGG_SORT    a CTA tile of pairs is radix-sorted by voxel key, then a
+ *                    warp segmented reduction sends one update per voxel;
+ *   SLIM_AGG_HASH    one-hot only: a CTA tile adds each pair at once into a
+ *                    shared-memory table keyed by (voxel, class), then sends
+ *                    one vector red.add per table entry;
+ *   SLIM_AGG_DIRECT  one-hot only: no grouping on chip, one vector red.add
+ *                    per pair, resolved in L2 (one thread per point);
+ *   SLIM_AGG_AUTO    one-hot: direct, or hash when tile_points is set;
+ *                    slim_autotune picks between direct and the hash tiles;
+ *                    soft counts: sort. */
+typedef enum {
+  SLIM_AGG_AUTO = 0,
+  SLIM_AGG_SORT = 1,
+  SLIM_AGG_HASH = 2,
+  SLIM_AGG_DIRECT = 3
+} slim_aggregation;
 
 typedef struct {
   float voxel_size;      /* metres, > 0 */
@@ -89,7 +98,7 @@ typedef struct {
   int64_t hash_capacity;   /* hash entries (rounded up to 32 x power of 2) */
   int64_t voxel_capacity;  /* SLIM_OPEN: maximum allocated voxels */
   int64_t max_points;      /* largest scan passed to slim_integrate */
-  int32_t aggregation;     /* slim_aggregation: how a tile groups its pairs */
+  int32_t aggregation;     /* slim_aggregation: how pairs reach the records */
   int32_t tile_points;     /* hash aggregation: points per CTA tile, 64, 128 or
                               256 (0 = 256); see slim_autotune */
 } slim_map_params;
@@ -178,6 +187,24 @@ slim_status slim_extract_tsdf(slim_map* m, int32_t* ijk_dev, float* D_dev, float
                               float* sem_dev, float* beta_dev, int32_t* index_dev,
                               int64_t cap, int64_t* n_out, int32_t flags, void* stream);
 
+/* Uncertainty read-out of the fused semantics, one row per allocated voxel
+ * in the order of slim_extract_tsdf, same two-call protocol (cap == 0 writes
+ * only *n_out). No counterpart in the paper's code; the quantities are the
+ * ones its Bayesian model defines:
+ *   closed set (Sec. III-C; Dirichlet posterior Dir(a), a_i = alpha0 + c_i,
+ *     A = sum a_i): unc_dev is n x (K + 1) float32: the variance of each
+ *     class probability, a_i (A - a_i) / (A^2 (A + 1)), then the entropy
+ *     -sum p_i ln p_i of the posterior predictive p_i = a_i / A
+ *     (Eq. dir_to_cat);
+ *   open set (Eq. student_t, with lambda = 2 nu = W): unc_dev is n x l
+ *     float32: the variance of the Student-t predictive of each element,
+ *     2 beta (W + 1) / (W (W - 2)), +inf where W <= 2 (the variance does
+ *     not exist for 2 nu <= 2).
+ * unc_dev is caller-owned device memory. The call synchronises `stream`.
+ * cap < *n_out returns SLIM_ERR_CAPACITY. */
+slim_status slim_extract_uncertainty(slim_map* m, float* unc_dev, int64_t cap, int64_t* n_out,
+                                     void* stream);
+
 /* Open-set read-out (end of Sec. III-D; Fig. "sit"): for every voxel row v
  * (0 .. voxels-1), cosine similarity s_vq = m_v . q_q / (|m_v| |q_q|) against
  * q queries (q_dev: q x l, bf16 bit patterns, row-major), softmax over the
@@ -246,13 +273,15 @@ typedef struct {
 slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items,
                                  void* stream);
 
-/* Tile-size autotuner (no counterpart in the paper). For a closed-set
- * one-hot map with hash aggregation, integrates the given scan (same
- * arguments as slim_integrate) repeatedly with every tile size (64, 128 and
- * 256 points per CTA), times each with CUDA events on `stream`, keeps the
- * fastest for this map and writes it to *best_tile (may be NULL). The map is
- * reset (emptied) before each trial and at the end. Synchronous. Other maps
- * return SLIM_ERR_UNSUPPORTED. */
+/* Strategy autotuner (no counterpart in the paper). For a closed-set one-hot
+ * map (aggregation AUTO, HASH or DIRECT), integrates 8 copies of the given
+ * scan (same arguments as slim_integrate) per launch with every candidate:
+ * direct reductions (AUTO, DIRECT) and hash tiles of 64, 128 and 256 points
+ * (AUTO, HASH); times each with CUDA events on `stream`, keeps the fastest
+ * for this map and writes it to *best_tile (0 = direct; may be NULL). The
+ * map is reset (emptied) before each trial and at the end. Synchronous.
+ * Soft-count, sort-aggregation and open-set maps return
+ * SLIM_ERR_UNSUPPORTED. */
 slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
                           const double pose_host[16], const void* sem_dev, void* stream,
                           int32_t* best_tile);

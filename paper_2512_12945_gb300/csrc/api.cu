@@ -142,10 +142,11 @@ slim_status check_params(const slim_map_params* p) {
   if (p->tile_points != 0 && p->tile_points != 64 && p->tile_points != 128 &&
       p->tile_points != 256)
     return fail(SLIM_ERR_ARG, "tile_points must be 0 (default), 64, 128 or 256");
-  if (p->aggregation < 0 || p->aggregation > 2)
-    return fail(SLIM_ERR_ARG, "aggregation must be 0 (auto), 1 (sort) or 2 (hash)");
-  if (p->aggregation == SLIM_AGG_HASH && p->mode != SLIM_CLOSED_ONEHOT)
-    return fail(SLIM_ERR_ARG, "hash aggregation serves the closed one-hot mode only");
+  if (p->aggregation < 0 || p->aggregation > 3)
+    return fail(SLIM_ERR_ARG, "aggregation must be 0 (auto), 1 (sort), 2 (hash) or 3 (direct)");
+  if ((p->aggregation == SLIM_AGG_HASH || p->aggregation == SLIM_AGG_DIRECT) &&
+      p->mode != SLIM_CLOSED_ONEHOT)
+    return fail(SLIM_ERR_ARG, "hash and direct aggregation serve the closed one-hot mode only");
   return SLIM_OK;
 }
 
@@ -200,6 +201,9 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   }
   m->tile_points = closed_tile_points(m->cap, m->band_blocks);
   m->hash_tile = p->tile_points > 0 ? p->tile_points : 256;
+  m->direct = p->mode == SLIM_CLOSED_ONEHOT &&
+              (p->aggregation == SLIM_AGG_DIRECT ||
+               (p->aggregation == SLIM_AGG_AUTO && p->tile_points == 0));
   m->n_entries = next_pow2((uint64_t)p->hash_capacity);
   const uint64_t nh = m->n_entries;
   const uint64_t bc = (uint64_t)p->block_capacity;
@@ -289,6 +293,16 @@ slim_status slim_map_destroy(slim_map* m) {
   return SLIM_OK;
 }
 
+// Closed one-hot map integrated by direct per-pair reductions.
+static bool uses_direct(const slim_map* m) {
+  return m->mode == SLIM_CLOSED_ONEHOT && m->direct;
+}
+
+// Closed one-hot map integrated by the shared-memory hash tiles.
+static bool uses_hash(const slim_map* m) {
+  return m->mode == SLIM_CLOSED_ONEHOT && !m->direct && m->p.aggregation != SLIM_AGG_SORT;
+}
+
 slim_status slim_map_reset(slim_map* m, void* stream) {
   if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
   cudaStream_t st = (cudaStream_t)stream;
@@ -324,7 +338,9 @@ slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
   const float* sem = static_cast<const float*>(sem_dev);
   if (m->mode != SLIM_OPEN) {
     const int tok = prof_begin(m, SLIM_KERNEL_FUSE_CLOSED, st);
-    if (m->mode == SLIM_CLOSED_ONEHOT && m->p.aggregation != SLIM_AGG_SORT)
+    if (uses_direct(m))
+      SLIM_CUDA(launch_fuse_direct(m->mv, g, pts_dev, sem, n, m->K, st));
+    else if (uses_hash(m))
       SLIM_CUDA(launch_fuse_hash(m->mv, g, pts_dev, sem, n, m->K, m->hash_tile, m->band_blocks,
                                  st));
     else
@@ -359,46 +375,83 @@ slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
                           int32_t* best_tile) {
   if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
   if (m->mode != SLIM_CLOSED_ONEHOT || m->p.aggregation == SLIM_AGG_SORT)
-    return fail(SLIM_ERR_UNSUPPORTED, "autotune serves closed one-hot maps with hash aggregation");
+    return fail(SLIM_ERR_UNSUPPORTED, "autotune serves closed one-hot maps (hash or direct)");
+  if (n < 1 || n > m->p.max_points) return fail(SLIM_ERR_ARG, "n must be in [1, max_points]");
+  if (!pts_dev || !sem_dev || !pose_host || !finite_pose(pose_host))
+    return fail(SLIM_ERR_ARG, "pts, sem or pose missing");
   cudaStream_t st = (cudaStream_t)stream;
-  const int saved = m->hash_tile;
+  // candidates: 0 = direct reductions, else hash tiles of that many points
+  int cand[4];
+  int nc = 0;
+  if (m->p.aggregation != SLIM_AGG_HASH) cand[nc++] = 0;
+  if (m->p.aggregation != SLIM_AGG_DIRECT) {
+    cand[nc++] = 64;
+    cand[nc++] = 128;
+    cand[nc++] = 256;
+  }
+  const int saved_tile = m->hash_tile;
+  const bool saved_direct = m->direct;
+  // each candidate integrates 8 copies of the scan per launch: the batched
+  // form in which the persistent and grid kernels run
+  HashBatch b;
+  b.n_jobs = 8;
+  b.work = m->mv.ctr + kCtrWork;
+  for (int k = 0; k < b.n_jobs; ++k) {
+    compose_pose(pose_host, m->p.body_from_sensor, b.job[k].g, m->p.voxel_size, m->p.trunc,
+                 m->p.min_range, m->p.max_range, m->cap);
+    b.job[k].mv = m->mv;
+    b.job[k].pts = pts_dev;
+    b.job[k].sem = static_cast<const float*>(sem_dev);
+    b.job[k].n = n;
+    b.job[k].K = m->K;
+    b.job[k].band_blocks = m->band_blocks;
+  }
   const bool prof = m->prof_on;
   m->prof_on = false;
   cudaEvent_t e0, e1;
   SLIM_CUDA(cudaEventCreate(&e0));
   SLIM_CUDA(cudaEventCreate(&e1));
-  const int cand[3] = {64, 128, 256};
   float best_ms = 1e30f;
-  int best = saved;
+  int best = saved_direct ? 0 : saved_tile;
   slim_status s = SLIM_OK;
-  for (int c = 0; c < 3 && s == SLIM_OK; ++c) {
-    m->hash_tile = cand[c];
+  for (int c = 0; c < nc && s == SLIM_OK; ++c) {
     if ((s = slim_map_reset(m, stream)) != SLIM_OK) break;
-    for (int w = 0; w < 3 && s == SLIM_OK; ++w) s = slim_integrate(m, pts_dev, n, pose_host, sem_dev, stream);
-    if (s != SLIM_OK) break;
-    cudaEventRecord(e0, st);
-    for (int r = 0; r < 5 && s == SLIM_OK; ++r) s = slim_integrate(m, pts_dev, n, pose_host, sem_dev, stream);
-    cudaEventRecord(e1, st);
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      s = cuda_fail(cudaGetLastError(), "autotune");
+    const int tile = cand[c];
+    auto launch = [&]() {
+      return tile == 0 ? launch_direct_batch(b, st) : launch_hash_batch(b, tile, 0, st);
+    };
+    cudaError_t e = cudaSuccess;
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "autotune");
       break;
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best_ms) {
       best_ms = ms;
-      best = cand[c];
+      best = tile;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   m->prof_on = prof;
-  m->hash_tile = s == SLIM_OK ? best : saved;
+  if (s == SLIM_OK) {
+    m->direct = best == 0;
+    if (best) m->hash_tile = best;
+  } else {
+    m->direct = saved_direct;
+    m->hash_tile = saved_tile;
+  }
   const slim_status r = slim_map_reset(m, stream);
   if (s != SLIM_OK) return s;
   if (r != SLIM_OK) return r;
   SLIM_CUDA(cudaStreamSynchronize(st));
-  if (best_tile) *best_tile = m->hash_tile;
+  if (best_tile) *best_tile = m->direct ? 0 : m->hash_tile;
   return SLIM_OK;
 }
 
@@ -447,12 +500,12 @@ slim_status slim_map_stats(slim_map* m, slim_stats* out, void* stream) {
   return SLIM_OK;
 }
 
-slim_status slim_extract_tsdf(slim_map* m, int32_t* ijk_dev, float* D_dev, float* W_dev,
-                              float* sem_dev, float* beta_dev, int32_t* index_dev, int64_t cap,
-                              int64_t* n_out, int32_t flags, void* stream) {
-  if (!m || !n_out) return fail(SLIM_ERR_ARG, "map or n_out is NULL");
-  if (cap < 0) return fail(SLIM_ERR_ARG, "cap must be >= 0");
-  cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+// The shared read-out pipeline: sort the allocated blocks by key, count the
+// voxels per block, scan, then write the requested outputs (a) in order.
+static slim_status extract_impl(slim_map* m, ExtractArgs a, int64_t cap, int64_t* n_out,
+                                cudaStream_t st) {
   slim_status s = read_counters(m, st);
   if (s != SLIM_OK) return s;
   if (m->pinned[kCtrStatus]) return status_of(m->pinned[kCtrStatus]);
@@ -463,22 +516,13 @@ slim_status slim_extract_tsdf(slim_map* m, int32_t* ijk_dev, float* D_dev, float
                            nb, 63, st));
   SLIM_CUDA(launch_extract_count(m->mv, m->ex_slots, nb, open, m->ex_counts, st));
   SLIM_CUDA(exclusive_scan_u32(m->ex_counts, m->ex_offs, nb, m->ex_tmp, st));
-  uint32_t total = 0;
   SLIM_CUDA(cudaMemcpyAsync(m->pinned + kCtrAux + 1, m->ex_offs + nb, sizeof(uint32_t),
                             cudaMemcpyDeviceToHost, st));
   SLIM_CUDA(cudaStreamSynchronize(st));
-  total = m->pinned[kCtrAux + 1];
+  const uint32_t total = m->pinned[kCtrAux + 1];
   *n_out = total;
   if (cap == 0) return SLIM_OK;
   if (cap < (int64_t)total) return fail(SLIM_ERR_CAPACITY, "cap smaller than the voxel count");
-  ExtractArgs a;
-  a.ijk = ijk_dev;
-  a.D = D_dev;
-  a.W = W_dev;
-  a.sem = sem_dev;
-  a.beta = open ? beta_dev : nullptr;
-  a.index = index_dev;
-  a.flags = flags;
   a.mode = m->mode;
   a.K = m->K;
   a.L = m->L;
@@ -487,6 +531,35 @@ slim_status slim_extract_tsdf(slim_map* m, int32_t* ijk_dev, float* D_dev, float
   SLIM_CUDA(launch_extract_write(m->mv, m->ex_slots, m->ex_keys, nb, m->ex_offs, a, st));
   SLIM_CUDA(cudaStreamSynchronize(st));
   return SLIM_OK;
+}
+
+extern "C" {
+
+slim_status slim_extract_tsdf(slim_map* m, int32_t* ijk_dev, float* D_dev, float* W_dev,
+                              float* sem_dev, float* beta_dev, int32_t* index_dev, int64_t cap,
+                              int64_t* n_out, int32_t flags, void* stream) {
+  if (!m || !n_out) return fail(SLIM_ERR_ARG, "map or n_out is NULL");
+  if (cap < 0) return fail(SLIM_ERR_ARG, "cap must be >= 0");
+  ExtractArgs a{};
+  a.ijk = ijk_dev;
+  a.D = D_dev;
+  a.W = W_dev;
+  a.sem = sem_dev;
+  a.beta = m->mode == SLIM_OPEN ? beta_dev : nullptr;
+  a.index = index_dev;
+  a.unc = nullptr;
+  a.flags = flags;
+  return extract_impl(m, a, cap, n_out, (cudaStream_t)stream);
+}
+
+slim_status slim_extract_uncertainty(slim_map* m, float* unc_dev, int64_t cap, int64_t* n_out,
+                                     void* stream) {
+  if (!m || !n_out) return fail(SLIM_ERR_ARG, "map or n_out is NULL");
+  if (cap < 0) return fail(SLIM_ERR_ARG, "cap must be >= 0");
+  if (cap > 0 && !unc_dev) return fail(SLIM_ERR_ARG, "unc_dev is NULL");
+  ExtractArgs a{};
+  a.unc = unc_dev;
+  return extract_impl(m, a, cap, n_out, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -556,7 +629,7 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
     if (b.n_jobs == 0) return SLIM_OK;
     slim_map* m0 = items[0].map;
     for (int32_t k = 0; k < n_items; ++k)
-      if (items[k].map->mode == SLIM_CLOSED_ONEHOT && items[k].map->p.aggregation != SLIM_AGG_SORT) {
+      if (uses_hash(items[k].map)) {
         m0 = items[k].map;
         break;
       }
@@ -566,12 +639,39 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
     b.n_jobs = 0;
     return e == cudaSuccess ? SLIM_OK : cuda_fail(e, "launch_hash_batch");
   };
+  // direct-reduction maps share one grid per 16 scans
+  HashBatch nb;
+  nb.n_jobs = 0;
+  slim_map* direct0 = nullptr;
+  auto flush_direct = [&]() -> slim_status {
+    if (nb.n_jobs == 0) return SLIM_OK;
+    const int tok = prof_begin(direct0, SLIM_KERNEL_BATCH, st);
+    cudaError_t e = launch_direct_batch(nb, st);
+    prof_end(direct0, tok, st);
+    nb.n_jobs = 0;
+    return e == cudaSuccess ? SLIM_OK : cuda_fail(e, "launch_direct_batch");
+  };
   for (int32_t k = 0; k < n_items; ++k) {
     const slim_batch_item& it = items[k];
     slim_map* m = it.map;
     m->scans++;
     if (it.n == 0) continue;
-    if (m->mode == SLIM_CLOSED_ONEHOT && m->p.aggregation != SLIM_AGG_SORT) {
+    if (uses_direct(m)) {
+      if (!direct0) direct0 = m;
+      HashJob& J = nb.job[nb.n_jobs++];
+      compose_pose(it.pose, m->p.body_from_sensor, J.g, m->p.voxel_size, m->p.trunc,
+                   m->p.min_range, m->p.max_range, m->cap);
+      J.mv = m->mv;
+      J.pts = it.pts_dev;
+      J.sem = static_cast<const float*>(it.sem_dev);
+      J.n = it.n;
+      J.K = m->K;
+      J.band_blocks = m->band_blocks;
+      if (nb.n_jobs == kMaxHashJobs) {
+        slim_status s = flush_direct();
+        if (s != SLIM_OK) return s;
+      }
+    } else if (uses_hash(m)) {
       if (b.n_jobs == 0) {
         b.work = m->mv.ctr + kCtrWork;
         tile = m->hash_tile;
@@ -595,6 +695,8 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
       if (s != SLIM_OK) return s;
     }
   }
+  slim_status s = flush_direct();
+  if (s != SLIM_OK) return s;
   return flush();
 }
 

@@ -1,7 +1,10 @@
 // Map export (read-out): every allocated voxel (W > 0) in block-key order,
 // then local order, with D = S / W, W and the semantic state; the closed-set
 // posterior predictive of Eq. (dir_to_cat), (alpha0 + c_i) / (K alpha0 + sum c),
-// is formed here on request.
+// is formed here on request, and so is the uncertainty read-out: the
+// variance of each class probability under the Dirichlet posterior and the
+// entropy of its predictive (closed set), or the variance of the Student-t
+// predictive of Eq. (student_t) with lambda = 2 nu = W (open set).
 #include <cuda_bf16.h>
 
 #include "block_sort.cuh"
@@ -93,6 +96,21 @@ __global__ void __launch_bounds__(256) k_extract_write(MapView mv, const uint32_
       if (a.D) a.D[o] = S / W;
       if (a.W) a.W[o] = W;
       if (a.index) a.index[o] = (int32_t)(slot * kBlockVoxels + l);
+      if (a.unc) {
+        // Dir(alpha~), alpha~_i = alpha0 + c_i, A = sum alpha~:
+        // Var theta_i = alpha~_i (A - alpha~_i) / (A^2 (A + 1)); entropy of p = alpha~ / A
+        float A = 0.f;
+        for (int k = 0; k < a.K; ++k) A += a.alpha0 + cnt[k * cs];
+        const float den = A * A * (A + 1.f);
+        float H = 0.f;
+        for (int k = 0; k < a.K; ++k) {
+          const float al = a.alpha0 + cnt[k * cs];
+          a.unc[o * (a.K + 1) + k] = al * (A - al) / den;
+          const float p = al / A;
+          if (p > 0.f) H -= p * logf(p);
+        }
+        a.unc[o * (a.K + 1) + a.K] = H;
+      }
       if (a.sem) {
         if (a.flags & SLIM_EXTRACT_POSTERIOR) {
           float tsum = 0.f;
@@ -115,6 +133,15 @@ __global__ void __launch_bounds__(256) k_extract_write(MapView mv, const uint32_
       if (a.beta)
         for (int k = 0; k < a.L; ++k)
           a.beta[o * a.L + k] = load_elem(mv.brow, (size_t)rw * a.L + k, a.bf16);
+      if (a.unc) {
+        // Student-t with 2 nu = W degrees of freedom: variance
+        // 2 beta (W + 1) / (W (W - 2)) for W > 2, else infinite
+        const float Wv = sw.y;
+        const float f = Wv > 2.f ? 2.f * (Wv + 1.f) / (Wv * (Wv - 2.f)) : INFINITY;
+        for (int k = 0; k < a.L; ++k)
+          a.unc[o * a.L + k] =
+              Wv > 2.f ? f * load_elem(mv.brow, (size_t)rw * a.L + k, a.bf16) : INFINITY;
+      }
     }
   }
 }

@@ -25,6 +25,7 @@
 // at most tau * 2^-21 (+ one FP32 rounding of the scale) per pair, and the
 // tile sum (at most TP pairs per entry) is exact in the 30-bit field.
 #include "block_sort.cuh"
+#include "closed_common.cuh"
 #include "common.cuh"
 #include "geometry.cuh"
 #include "hash.cuh"
@@ -44,13 +45,6 @@ struct HashTile {
   // accumulator a (key, count) u32 pair and a u32 sum; counters
   static constexpr size_t kSmem = (size_t)kTbl * 14 + (size_t)kVc * 12 + 16 * 4;
 };
-
-// Bucket of a block key in the tile's block table (a cheap 32-bit mix: the
-// table holds a few dozen keys per tile).
-__device__ __forceinline__ uint32_t tile_hash(uint64_t kb) {
-  uint32_t h = ((uint32_t)kb * 0x9E3779B1u) ^ ((uint32_t)(kb >> 32) * 0x85EBCA77u);
-  return h ^ (h >> 15);
-}
 
 // Insert-or-find a block key; the thread that inserts it appends the entry
 // to the tile's block list. Returns the entry, or 0xFFFFFFFF when full.
@@ -114,72 +108,6 @@ __device__ __forceinline__ bool vc_add(uint32_t* vkc, uint32_t* vsum, uint32_t k
   return false;
 }
 
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Index of the largest of K probabilities (ties to the lowest index). The
-// loads of a group of 16 are issued together before any comparison.
-__device__ __forceinline__ uint32_t argmax_row(const float* __restrict__ row, int K) {
-  float bv = -INFINITY;
-  uint32_t best = 0;
-  if ((K & 3) == 0 && (reinterpret_cast<uintptr_t>(row) & 15) == 0) {
-    const float4* r4 = reinterpret_cast<const float4*>(row);
-    const int K4 = K >> 2;
-    for (int c = 0; c < K4; c += 4) {
-      float4 v[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        v[q] = (c + q < K4) ? __ldg(r4 + c + q) : make_float4(-INFINITY, -INFINITY, -INFINITY,
-                                                               -INFINITY);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int k = 4 * (c + q) + u;
-          if (k < K && (k == 0 || e[u] > bv)) {
-            bv = e[u];
-            best = (uint32_t)k;
-          }
-        }
-      }
-    }
-  } else {
-    for (int c = 0; c < K; c += 8) {
-      float v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = (c + q < K) ? __ldg(row + c + q) : -INFINITY;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = c + q;
-        if (k < K && (k == 0 || v[q] > bv)) {
-          bv = v[q];
-          best = (uint32_t)k;
-        }
-      }
-    }
-  }
-  return best;
-}
-
-// One tile: points [tile * tile_points, (tile + 1) * tile_points) of a scan.
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-__device__ __forceinline__ int job_of(const HashBatch& b, uint32_t t) {
-  int jb = 0;
-  while (jb + 1 < b.n_jobs && t >= b.job[jb + 1].tile_begin) ++jb;
-  return jb;
-}
-
 // Ask L2 for this thread's point and probability row of tile t (the tile the
 // CTA takes next), so that its loads at the start of that tile hit L2.
 __device__ __forceinline__ void prefetch_tile(const HashBatch& b, uint32_t t) {
@@ -192,6 +120,7 @@ __device__ __forceinline__ void prefetch_tile(const HashBatch& b, uint32_t t) {
   prefetch_l2(row + J.K - 1);
 }
 
+// One tile: points [tile * tile_points, (tile + 1) * tile_points) of a scan.
 template <int TP>
 __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom& g,
                                                const float* __restrict__ pts,

@@ -37,6 +37,10 @@ struct HashBatch {
 };
 cudaError_t launch_hash_batch(HashBatch& b, int tile, int ctas_per_sm, cudaStream_t st);
 cudaError_t hash_setup_attributes();
+// Direct per-pair reductions, one scan / the jobs of b in one grid.
+cudaError_t launch_fuse_direct(const MapView& mv, const ScanGeom& g, const float* pts,
+                               const float* sem, int64_t n, int K, cudaStream_t st);
+cudaError_t launch_direct_batch(HashBatch& b, cudaStream_t st);
 // Zero the records of the blocks allocated so far (closed-set maps).
 cudaError_t launch_zero_used_blocks(const MapView& mv, cudaStream_t st);
 cudaError_t launch_fuse_hash(const MapView& mv, const ScanGeom& g, const float* pts,
@@ -73,6 +77,7 @@ struct ExtractArgs {
   float* sem;
   float* beta;
   int32_t* index;
+  float* unc;        // uncertainty read-out (closed n x (K+1), open n x l) or null
   int32_t flags;
   int32_t mode;
   int32_t K;

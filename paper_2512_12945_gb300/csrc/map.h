@@ -38,6 +38,7 @@ struct slim_map {
   int K = 0, L = 0, mode = 0, bf16 = 0, rs = 0;
   int cap = 0, band_blocks = 0, tile_points = 0;
   int hash_tile = 256;  // threads (points) per CTA of the hash-aggregation kernel
+  bool direct = false;  // closed one-hot: direct per-pair reductions instead of hash tiles
   uint64_t n_entries = 0;
   slim::MapView mv{};
   std::vector<void*> allocs;

@@ -10,9 +10,13 @@
 //   warp 1      one thread issues tcgen05.mma (kind::f16, BF16 in, FP32
 //               accumulate, M = 128, N = queries rounded up to 16) into one of
 //               two TMEM accumulators, and tcgen05.commit frees each stage;
-//   warps 2-5   epilogue: tcgen05.ld of the accumulator rows (one voxel per
-//               thread), cosine = dot / (|m| |q|), online softmax, argmax,
-//               threshold; the accumulator is released for the next tile.
+//   warps 2-9   epilogue, two warps per TMEM lane quarter (one voxel row per
+//               thread): each takes every other 32-column chunk of the
+//               accumulator (tcgen05.ld), cosine = dot / (|m| |q|), online
+//               softmax in base 2 with the chunk's maximum and sum taken by
+//               trees, argmax; the odd-chunk warp hands its (max, sum,
+//               argmax) to the even-chunk warp through shared memory, which
+//               combines them, applies the threshold and writes the row.
 //
 // The grid is persistent (one CTA per SM, tiles strided over CTAs). Every
 // mbarrier wait is bounded: running out raises the map status, the CTA stops
@@ -30,7 +34,7 @@ namespace slim {
 constexpr int kQM = 128;        // voxel rows per tile
 constexpr int kQK = 64;         // K elements per stage (128-byte rows)
 constexpr int kQStages = 4;
-constexpr int kQThreads = 192;  // 6 warps
+constexpr int kQThreads = 320;  // 10 warps: TMA, MMA, 8 epilogue
 constexpr uint64_t kWaitNs = 500ull * 1000 * 1000;  // a wait gives up after 0.5 s
 
 struct QueryArgs {
@@ -40,6 +44,7 @@ struct QueryArgs {
   int32_t N;         // Q rounded up to 16
   uint32_t tmem_cols;
   float inv_temp;
+  float temp_log2e;     // T / log2(e): turns a base-2 logit back into a cosine
   float tp;
   const float* qinv;    // [Q] 1 / |q|
   const float* rnorm2;  // [n_rows] |m|^2
@@ -128,6 +133,86 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// 32 consecutive accumulator columns of this thread's TMEM lane; the values
+// may be used only after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Online softmax over one chunk of W accumulator columns [c0, c0 + W) of a
+// row: x = acc * colscale[c] * rowscale are base-2 logits (cos / T times
+// log2 e); columns >= Q are ignored. The chunk's maximum (with the lowest
+// index among ties) is found by a tree, then its W exponentials are
+// independent, so the chain per chunk is short.
+template <int W>
+__device__ __forceinline__ void softmax_chunk(const uint32_t (&r)[W], int c0, int Q,
+                                              const float* colscale, float rowscale, float* scores,
+                                              float cosscale, float& mrun, float& srun, int& best) {
+  float x[W];
+  int ix[W];
+  const float4* cs4 = reinterpret_cast<const float4*>(colscale + c0);  // c0 % 16 == 0
+#pragma unroll
+  for (int j4 = 0; j4 < W / 4; ++j4) {
+    const float4 cv = cs4[j4];
+    const float cj[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * j4 + u, c = c0 + j;
+      const float acc = __uint_as_float(r[j]);
+      x[j] = c < Q ? acc * cj[u] * rowscale : -INFINITY;
+      ix[j] = c;
+      if (scores && c < Q) scores[c] = acc * cj[u] * cosscale;
+    }
+  }
+  float mx[W];
+  int bi[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    mx[j] = x[j];
+    bi[j] = ix[j];
+  }
+#pragma unroll
+  for (int w = W / 2; w > 0; w >>= 1) {
+#pragma unroll
+    for (int j = 0; j < w; ++j) {
+      const bool take = mx[j + w] > mx[j];  // ties keep the lower index
+      bi[j] = take ? bi[j + w] : bi[j];
+      mx[j] = take ? mx[j + w] : mx[j];
+    }
+  }
+  const float mnew = fmaxf(mrun, mx[0]);
+  if (mx[0] > mrun) best = bi[0];
+  float e[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) e[j] = ex2_approx(x[j] - mnew);
+#pragma unroll
+  for (int w = W / 2; w > 0; w >>= 1) {
+#pragma unroll
+    for (int j = 0; j < w; ++j) e[j] += e[j + w];
+  }
+  srun = srun * ex2_approx(mrun - mnew) + e[0];
+  mrun = mnew;
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -154,15 +239,22 @@ __global__ void __launch_bounds__(kQThreads, 1)
   uint64_t* empty = bars + kQStages;
   uint64_t* tfull = bars + 2 * kQStages;
   uint64_t* tempty = bars + 2 * kQStages + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kQStages + 4);
+  uint64_t* hdone = bars + 2 * kQStages + 4;  // [quarter][accumulator]: odd half handed over
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kQStages + 12);
   volatile uint32_t* abort_flag = tmem_slot + 1;
-  float* s_qinv = reinterpret_cast<float*>(tmem_slot + 2);
+  float* s_qinv = reinterpret_cast<float*>(tmem_slot + 4);
+  float* part_m = s_qinv + 256;  // [accumulator][128 rows]: odd half's running max
+  float* part_s = part_m + 256;  //                          running sum
+  int* part_b = reinterpret_cast<int*>(part_s + 256);  //   argmax
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t num_tiles = (a.n_rows + kQM - 1) / kQM;
   const int kchunks = a.L / kQK;
 
-  for (int c = threadIdx.x; c < a.N; c += kQThreads) s_qinv[c] = c < a.Q ? a.qinv[c] : 0.f;
+  // per query column: 1 / |q| * log2(e) / T (the scores output divides the
+  // log2(e) / T factor back out)
+  for (int c = threadIdx.x; c < a.N; c += kQThreads)
+    s_qinv[c] = c < a.Q ? a.qinv[c] * (a.inv_temp * 1.4426950408889634f) : 0.f;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kQStages; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
@@ -170,8 +262,9 @@ __global__ void __launch_bounds__(kQThreads, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(smem_u32(&tfull[s]), 1);
-      mbar_init(smem_u32(&tempty[s]), 4);
+      mbar_init(smem_u32(&tempty[s]), 8);
     }
+    for (int s = 0; s < 8; ++s) mbar_init(smem_u32(&hdone[s]), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
@@ -275,13 +368,15 @@ __global__ void __launch_bounds__(kQThreads, 1)
     if (committed_any) mbar_wait(last_commit_bar, last_commit_phase);
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue
-    const int quarter = warp & 3;
+    const int quarter = warp & 3;      // the TMEM lane quarter this warp may read
+    const int half = (warp - 2) >> 2;  // 0: even 32-column chunks, 1: odd ones
+    const int rl = quarter * 32 + lane;
     int acc = 0;
     uint32_t acc_phase = 0;
     for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
       bool ok = mbar_wait(smem_u32(&tfull[acc]), acc_phase);
       ok = __all_sync(0xFFFFFFFFu, ok);
-      if (!ok || *abort_flag) {
+      if (!ok) {
         if (lane == 0) {
           *abort_flag = 1;
           raise_status(a.status, kDevTimeout, 23);
@@ -289,44 +384,85 @@ __global__ void __launch_bounds__(kQThreads, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t row = tile * kQM + quarter * 32 + lane;
+      const uint32_t row = tile * kQM + rl;
       const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * a.N);
       const float n2 = row < a.n_rows ? a.rnorm2[row] : 0.f;
       const float rinv = n2 > 0.f ? rsqrtf(n2) : 0.f;
-      const float sc = rinv * a.inv_temp;
+      float* srow = (a.scores && row < a.n_rows) ? a.scores + (size_t)row * a.Q : nullptr;
+      // base-2 logits: colscale = |q|^-1 log2(e) / T, rowscale = |m|^-1
       float mrun = -INFINITY, srun = 0.f;
       int best = -1;
-      for (int c0 = 0; c0 < a.N; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(taddr + (uint32_t)c0, r);
+      // full 32-column chunks of this half, the next one's TMEM load in
+      // flight while the current one is reduced; then the 16-wide tail
+      const int nfull = a.N / 32;
+      int ch = half;
+      if (ch < nfull) {
+        uint32_t ra[32], rb[32];
+        tmem_ld32_async(taddr + (uint32_t)(ch * 32), ra);
+        tmem_wait_ld();
+        for (;;) {
+          const int nx = ch + 2;
+          if (nx < nfull) tmem_ld32_async(taddr + (uint32_t)(nx * 32), rb);
+          softmax_chunk<32>(ra, ch * 32, a.Q, s_qinv, rinv, srow, rinv * a.temp_log2e, mrun,
+                            srun, best);
+          if (nx >= nfull) break;
+          tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int c = c0 + j;
-          if (c >= a.Q) break;
-          const float cosv = __uint_as_float(r[j]) * s_qinv[c] * rinv;
-          if (a.scores && row < a.n_rows) a.scores[(size_t)row * a.Q + c] = cosv;
-          const float x = cosv * a.inv_temp;
-          if (x > mrun) {
-            srun = srun * __expf(mrun - x) + 1.f;
-            mrun = x;
-            best = c;
-          } else {
-            srun += __expf(x - mrun);
-          }
+          for (int j = 0; j < 32; ++j) ra[j] = rb[j];
+          ch = nx;
         }
+        ch += 2;
       }
-      (void)sc;
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
-      if (row < a.n_rows) {
-        if (n2 > 0.f) {
-          const float p = 1.f / srun;
-          a.prob[row] = p;
-          a.label[row] = p >= a.tp ? best : -1;
-        } else {
-          a.prob[row] = 0.f;
-          a.label[row] = -1;
+      if (ch == nfull && nfull * 32 < a.N) {  // N is a multiple of 16
+        uint32_t r[16];
+        tmem_ld16(taddr + (uint32_t)(nfull * 32), r);
+        softmax_chunk<16>(r, nfull * 32, a.Q, s_qinv, rinv, srow, rinv * a.temp_log2e, mrun,
+                          srun, best);
+      }
+      const uint32_t hbar = smem_u32(&hdone[quarter * 2 + acc]);
+      if (half == 1) {
+        part_m[acc * kQM + rl] = mrun;
+        part_s[acc * kQM + rl] = srun;
+        part_b[acc * kQM + rl] = best;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(smem_u32(&tempty[acc]));
+          mbar_arrive(hbar);
+        }
+      } else {
+        bool ok2 = mbar_wait(hbar, acc_phase);
+        ok2 = __all_sync(0xFFFFFFFFu, ok2);
+        if (ok2) {
+          // combine with the odd half: lowest index among equal maxima
+          const float m1 = part_m[acc * kQM + rl], s1 = part_s[acc * kQM + rl];
+          const int b1 = part_b[acc * kQM + rl];
+          const float m = fmaxf(mrun, m1);
+          srun = srun * ex2_approx(mrun - m) + s1 * ex2_approx(m1 - m);
+          if (m1 > mrun || (m1 == mrun && b1 >= 0 && b1 < best)) best = b1;
+          mrun = m;
+        }
+        // the shared partials are read: the accumulator and this slot of
+        // the hand-over may be reused
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
+        if (!ok2) {
+          if (lane == 0) {
+            *abort_flag = 1;
+            raise_status(a.status, kDevTimeout, 24);
+          }
+          break;
+        }
+        if (row < a.n_rows) {
+          if (n2 > 0.f) {
+            const float p = 1.f / srun;
+            a.prob[row] = p;
+            a.label[row] = p >= a.tp ? best : -1;
+          } else {
+            a.prob[row] = 0.f;
+            a.label[row] = -1;
+          }
         }
       }
       if (++acc == 2) {
@@ -427,8 +563,8 @@ static bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t
 }
 
 size_t query_smem_bytes(int N) {
-  return 1024 + (size_t)kQStages * (kQM * 128 + (size_t)N * 128) + (2 * kQStages + 4) * 8 + 16 +
-         256 * 4;
+  return 1024 + (size_t)kQStages * (kQM * 128 + (size_t)N * 128) + (2 * kQStages + 12) * 8 + 16 +
+         256 * 4 + 3 * 256 * 4;
 }
 
 cudaError_t query_setup_attributes() {
@@ -467,6 +603,7 @@ slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float tempe
   a.N = N;
   a.tmem_cols = cols;
   a.inv_temp = 1.f / temperature;
+  a.temp_log2e = temperature / 1.4426950408889634f;
   a.tp = tp;
   a.qinv = m->qscratch.qinv;
   a.rnorm2 = rn2;
@@ -578,6 +715,7 @@ extern "C" slim_status slim_query_rows_static(const uint16_t* rows_dev, int64_t 
   a.N = N;
   a.tmem_cols = cols;
   a.inv_temp = 1.f / temperature;
+  a.temp_log2e = temperature / 1.4426950408889634f;
   a.tp = tp;
   a.qinv = qinv;
   a.rnorm2 = rnorm2;

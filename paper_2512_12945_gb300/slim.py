@@ -21,7 +21,7 @@ from . import build as _build
 SLIM_CLOSED_ONEHOT, SLIM_CLOSED_SOFT, SLIM_OPEN = 0, 1, 2
 SLIM_STORE_F32, SLIM_STORE_BF16 = 0, 1
 SLIM_EXTRACT_POSTERIOR = 1
-AGGREGATION = {"auto": 0, "sort": 1, "hash": 2}
+AGGREGATION = {"auto": 0, "sort": 1, "hash": 2, "direct": 3}
 MODES = {"onehot": SLIM_CLOSED_ONEHOT, "soft": SLIM_CLOSED_SOFT, "open": SLIM_OPEN}
 STATUS = {0: "SLIM_OK", 1: "SLIM_ERR_ARG", 2: "SLIM_ERR_CUDA", 3: "SLIM_ERR_CAPACITY",
           4: "SLIM_ERR_TIMEOUT", 5: "SLIM_ERR_NOMEM", 6: "SLIM_ERR_UNSUPPORTED",
@@ -60,7 +60,7 @@ EXPORTS = ["slim_map_params_default", "slim_map_create", "slim_map_destroy", "sl
            "slim_integrate", "slim_integrate_host", "slim_map_sync", "slim_map_stats",
            "slim_extract_tsdf", "slim_query", "slim_backward", "slim_integrate_batch",
            "slim_profile_enable", "slim_profile_read", "slim_autotune", "slim_query_rows_static",
-           "slim_last_error"]
+           "slim_extract_uncertainty", "slim_last_error"]
 KERNELS = ["traverse", "fuse_closed", "open_pairs", "open_apply", "query", "backward", "batch",
            "reset"]
 
@@ -101,6 +101,7 @@ def lib():
             "slim_profile_read": [P, P, P],
             "slim_autotune": [P, P, I64, P, P, P, ctypes.POINTER(I32)],
             "slim_query_rows_static": [P, I64, I32, P, I32, F, F, P, P, P],
+            "slim_extract_uncertainty": [P, P, I64, ctypes.POINTER(I64), P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -216,6 +217,22 @@ def slim_extract_tsdf(h, mode, width, posterior=False, index=False, stream=None,
                                    ptr("index"), max(cnt, 1), ctypes.byref(n), flags, st),
            "slim_extract_tsdf")
     return out
+
+
+def slim_extract_uncertainty(h, mode, width, stream=None, device=None):
+    """Closed set: (n, K+1) class-probability variances + predictive entropy;
+    open set: (n, l) Student-t predictive variances (inf where W <= 2)."""
+    n = ctypes.c_int64(0)
+    st = _stream(stream)
+    _check(lib().slim_extract_uncertainty(h, None, 0, ctypes.byref(n), st),
+           "slim_extract_uncertainty(size)")
+    cnt = n.value
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    w = width if mode == SLIM_OPEN else width + 1
+    unc = torch.empty((cnt, w), dtype=torch.float32, device=dev)
+    _check(lib().slim_extract_uncertainty(h, ctypes.c_void_p(unc.data_ptr()), max(cnt, 1),
+                                          ctypes.byref(n), st), "slim_extract_uncertainty")
+    return unc
 
 
 def slim_query(h, q_bf16, temperature, tp, n_rows, scores=False, stream=None):
@@ -370,6 +387,9 @@ class Map:
 
     def extract(self, posterior=False, index=False, stream=None):
         return slim_extract_tsdf(self.handle, self.mode, self.width, posterior, index, stream)
+
+    def uncertainty(self, stream=None):
+        return slim_extract_uncertainty(self.handle, self.mode, self.width, stream)
 
     def query(self, q_bf16, temperature=0.01, tp=0.1, scores=False, stream=None):
         rows = self.stats(stream)["voxels"]

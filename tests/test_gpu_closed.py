@@ -18,7 +18,7 @@ def _built():
     build.build()
 
 
-@pytest.mark.parametrize("agg", ["sort", "hash"])
+@pytest.mark.parametrize("agg", ["sort", "hash", "direct"])
 def test_room_lidar_onehot(agg):
     w = synth.room_lidar(n_scans=10)
     g = to_np(gpu_map(w, aggregation=agg).extract())
@@ -38,7 +38,8 @@ def test_room_posterior_and_alpha0():
         assert_close(g["sem"].sum(1), np.ones(len(g["W"])), 1e-5, 1e-6, "posterior sum")
 
 
-@pytest.mark.parametrize("agg,tile", [("sort", 0), ("hash", 64), ("hash", 128), ("hash", 256)])
+@pytest.mark.parametrize("agg,tile", [("sort", 0), ("hash", 64), ("hash", 128), ("hash", 256),
+                                      ("direct", 0)])
 def test_street_lidar_reduced(agg, tile):
     w = synth.street_lidar(n_scans=4, n_beams=64, n_az=512)
     g = to_np(gpu_map(w, aggregation=agg, tile_points=tile).extract())
@@ -53,7 +54,7 @@ def test_soft_counts():
     compare_closed(g, o, "soft")
 
 
-@pytest.mark.parametrize("agg", ["sort", "hash"])
+@pytest.mark.parametrize("agg", ["sort", "hash", "direct"])
 def test_ragged_empty_and_invalid(agg):
     """n = 0, single points, a ragged tail, NaN / out-of-range points."""
     w = synth.room_lidar(n_scans=2, n_beams=16, n_az=64)
@@ -81,7 +82,7 @@ def test_empty_map_extract():
     assert ext["W"].shape[0] == 0
 
 
-@pytest.mark.parametrize("agg", ["sort", "hash"])
+@pytest.mark.parametrize("agg", ["sort", "hash", "direct"])
 def test_block_capacity_fault_is_reported(agg):
     """Too few blocks: the sticky status reports SLIM_ERR_CAPACITY; nothing hangs."""
     from paper_2512_12945_gb300 import slim
@@ -158,8 +159,30 @@ def test_autotune_picks_a_tile_and_resets():
                  max_range=w.max_range, body_from_sensor=w.body_from_sensor, max_points=131072)
     pts, sem = torch.from_numpy(s["pts"]).cuda(), torch.from_numpy(s["sem"]).cuda()
     best = m.autotune(pts, s["pose"], sem)
-    assert best in (64, 128, 256)
+    assert best in (0, 64, 128, 256)  # 0: direct reductions
     assert m.stats()["blocks"] == 0
     for sc in w.scans:
         m.integrate(torch.from_numpy(sc["pts"]).cuda(), sc["pose"], torch.from_numpy(sc["sem"]).cuda())
     compare_closed(to_np(m.extract()), oracle_map(w).extract(), "onehot")
+
+
+def test_direct_batch_matches_oracle():
+    """Direct per-pair reductions through slim_integrate_batch (all scans of
+    two maps in shared grids) give the oracle's map."""
+    from paper_2512_12945_gb300 import slim
+    w = synth.street_lidar(n_scans=3, n_az=512)
+    r = synth.room_lidar(n_scans=3)
+    maps, items = [], []
+    for wk in (w, r):
+        m = slim.Map(voxel_size=wk.voxel_size, trunc=wk.trunc, num_classes=wk.num_classes,
+                     min_range=wk.min_range, max_range=wk.max_range,
+                     body_from_sensor=wk.body_from_sensor,
+                     max_points=max(s["pts"].shape[0] for s in wk.scans), aggregation="direct")
+        maps.append(m)
+        for s in wk.scans:
+            items.append((m, torch.from_numpy(s["pts"]).cuda(), s["pose"],
+                          torch.from_numpy(s["sem"]).cuda()))
+    slim.slim_integrate_batch(items)
+    for m, wk in zip(maps, (w, r)):
+        m.sync()
+        compare_closed(to_np(m.extract()), oracle_map(wk).extract(), "onehot")

@@ -46,7 +46,8 @@ def _run(storage, dim, Q, frames=3, wh=(64, 48), T=0.01, tp=0.1):
 
 
 @pytest.mark.parametrize("storage,dim,Q", [("bf16", 64, 256), ("f32", 64, 37),
-                                           ("bf16", 512, 256), ("f32", 512, 16)])
+                                           ("bf16", 512, 256), ("f32", 512, 16),
+                                           ("bf16", 128, 200)])
 def test_query_matches_oracle_readout(storage, dim, Q):
     _, ext, (gl, gp, gs), (ol, op, oc), _, _ = _run(storage, dim, Q)
     assert gs.shape == oc.shape
