@@ -73,6 +73,13 @@ def _load():
             lib.ora_extract.argtypes = [P, P, P, P, P, P, ctypes.c_int32]
             lib.ora_uncertainty.restype = ctypes.c_int64
             lib.ora_uncertainty.argtypes = [P, P]
+            F = ctypes.c_float
+            lib.ora_render.restype = ctypes.c_int64
+            lib.ora_render.argtypes = [P, P, F, F, F, F, ctypes.c_int32, ctypes.c_int32, F, F,
+                                       P, P, P, P, P]
+            lib.ora_pixel_visits.restype = ctypes.c_int64
+            lib.ora_pixel_visits.argtypes = [F, P, F, F, F, F, ctypes.c_int32, ctypes.c_int32,
+                                             F, F, P, ctypes.c_int64]
             lib.ora_query.restype = None
             lib.ora_query.argtypes = [P, ctypes.c_int64, ctypes.c_int32, P, ctypes.c_int32,
                                       ctypes.c_double, ctypes.c_double, P, P, P]
@@ -169,6 +176,21 @@ class OracleMap:
         self.lib.ora_uncertainty(self.h, _ptr(unc))
         return unc
 
+    def render(self, world_from_camera, fx, fy, cx, cy, width, height, near, far, q=None):
+        """Ray-cast render from a pinhole camera: dict of depth (H, W) f64
+        (+inf on a miss), ijk (H, W, 3) int32 of the voxel after the zero
+        crossing (INT32_MIN on a miss), label (H, W) int32 (closed set), and
+        sim (H, W) f64 (open set with a query q)."""
+        depth = np.zeros((height, width))
+        ijk = np.zeros((height, width, 3), np.int32)
+        label = np.zeros((height, width), np.int32)
+        sim = np.zeros((height, width))
+        qq = None if q is None else _f32(q).reshape(-1)
+        self.lib.ora_render(self.h, _ptr(_pose(world_from_camera)), fx, fy, cx, cy, width,
+                            height, near, far, None if qq is None else _ptr(qq), _ptr(depth),
+                            _ptr(ijk), _ptr(label), _ptr(sim))
+        return dict(depth=depth, ijk=ijk, label=label, sim=sim)
+
     def backward_scan(self, pts, pose, sem, gD, gS, gB=None):
         """Per-point dL/dsem (n,w) and dL/dxyz (n,3); call extract() first."""
         pts = _f32(pts, 3)
@@ -212,6 +234,17 @@ def point_visits(params, pt, pose):
     n = lib.ora_point_visits(ctypes.byref(params), _ptr(pt), _ptr(pose), _ptr(ijk), cap)
     if n < 0:
         return None
+    assert n <= cap
+    return ijk[:n].copy()
+
+
+def pixel_visits(voxel_size, world_from_camera, fx, fy, cx, cy, px, py, near, far):
+    """Voxels the render ray of pixel (px, py) enters, in order."""
+    lib = _load()
+    cap = 1 << 16
+    ijk = np.zeros((cap, 3), np.int32)
+    n = lib.ora_pixel_visits(voxel_size, _ptr(_pose(world_from_camera)), fx, fy, cx, cy, px, py,
+                             near, far, _ptr(ijk), cap)
     assert n <= cap
     return ijk[:n].copy()
 

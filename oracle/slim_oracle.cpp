@@ -518,6 +518,178 @@ int64_t ora_uncertainty(void* h, double* unc) {
   return (int64_t)order.size();
 }
 
+// ----------------------------------------------------------------- render
+// Voxels a ray o + t u enters for t in [t0, t1], in order (Amanatides & Woo,
+// the same FP32 operation order as the band traversal of point_pairs_f32,
+// ties to the lowest axis), at most cap of them.
+void ray_visits_f32(float v, const float o[3], const float u[3], float t0, float t1, int cap,
+                    std::vector<std::array<int32_t, 3>>* out) {
+  int32_t ii[3], step[3];
+  float tMax[3], tDelta[3];
+  for (int a = 0; a < 3; ++a) {
+    float tu = t0 * u[a];
+    float s = o[a] + tu;
+    float sv = s / v;
+    ii[a] = (int32_t)std::floor(sv);
+    step[a] = u[a] > 0.0f ? 1 : (u[a] < 0.0f ? -1 : 0);
+    if (u[a] != 0.0f) {
+      tDelta[a] = v / std::fabs(u[a]);
+      float bnd = (float)(ii[a] + (step[a] > 0 ? 1 : 0)) * v;
+      float gap = bnd - s;
+      float dt = gap / u[a];
+      tMax[a] = t0 + dt;
+    } else {
+      tDelta[a] = INFINITY;
+      tMax[a] = INFINITY;
+    }
+  }
+  for (int k = 0; k < cap; ++k) {
+    out->push_back({ii[0], ii[1], ii[2]});
+    int a = 0;
+    if (tMax[1] < tMax[a]) a = 1;
+    if (tMax[2] < tMax[a]) a = 2;
+    if (tMax[a] > t1) break;
+    ii[a] += step[a];
+    tMax[a] = tMax[a] + tDelta[a];
+  }
+}
+
+// Unit-length camera ray of pixel (px, py) of a pinhole camera (x right,
+// y down, looking along +z), rotated into the world: FP32, fixed op order.
+void pixel_ray_f32(const float R[9], float fx, float fy, float cx, float cy, int32_t px,
+                   int32_t py, float u[3]) {
+  float ax = (float)px + 0.5f;
+  float ay = (float)py + 0.5f;
+  float dx = (ax - cx) / fx;
+  float dy = (ay - cy) / fy;
+  float n2 = dx * dx;
+  float m2 = dy * dy;
+  n2 = n2 + m2;
+  n2 = n2 + 1.0f;
+  float nn = std::sqrt(n2);
+  float d[3] = {dx / nn, dy / nn, 1.0f / nn};
+  for (int a = 0; a < 3; ++a) {
+    float m0 = R[a * 3 + 0] * d[0];
+    float m1 = R[a * 3 + 1] * d[1];
+    float m2a = R[a * 3 + 2] * d[2];
+    float s = m0 + m1;
+    u[a] = s + m2a;
+  }
+}
+
+// Ray-cast render of the map from a pinhole camera (Sec. III-E: the map is
+// rendered from a camera viewpoint instead of being meshed). Per pixel
+// (row-major), the ray from the camera centre enters voxels for t in
+// [near, far] (at most 3 ceil((far - near) / v) + 3 of them). A voxel is
+// observed when the map holds it; its ray parameter is the projection of
+// its centre, t_c = (c - o) . u (FP32). The surface is the first pair of
+// consecutive entered voxels, both observed, with D_prev > 0 >= D: depth =
+// t_prev + (t_c - t_prev) D_prev / (D_prev - D). Outputs at that voxel
+// (the one with D <= 0): its indices, the closed-set label (the largest
+// count, ties to the lowest class) or -1 for the open set, and for the open
+// set with a query q the cosine m . q / (|m| |q|) (0 for a zero norm).
+// A pixel without a crossing gets depth +inf, indices INT32_MIN, label -1,
+// sim 0.
+int64_t ora_render(void* h, const double world_from_camera[16], float fx, float fy, float cx,
+                   float cy, int32_t width, int32_t height, float near_t, float far_t,
+                   const float* q, double* depth, int32_t* ijk, int32_t* label, double* sim) {
+  Map& m = *(Map*)h;
+  const Params& P = m.p;
+  const float v = P.voxel_size;
+  float R[9], o[3];
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) R[a * 3 + b] = (float)world_from_camera[a * 4 + b];
+    o[a] = (float)world_from_camera[a * 4 + 3];
+  }
+  const int cap = 3 * (int)std::ceil(((double)far_t - (double)near_t) / (double)v) + 3;
+  const int w = sem_width(P);
+  double qn = 0.0;
+  if (q)
+    for (int c = 0; c < w; ++c) qn += (double)q[c] * (double)q[c];
+  qn = std::sqrt(qn);
+  int64_t hits = 0;
+  std::vector<std::array<int32_t, 3>> vis;
+  for (int32_t py = 0; py < height; ++py)
+    for (int32_t px = 0; px < width; ++px) {
+      const int64_t pix = (int64_t)py * width + px;
+      depth[pix] = INFINITY;
+      ijk[3 * pix + 0] = ijk[3 * pix + 1] = ijk[3 * pix + 2] = INT32_MIN;
+      label[pix] = -1;
+      if (sim) sim[pix] = 0.0;
+      float u[3];
+      pixel_ray_f32(R, fx, fy, cx, cy, px, py, u);
+      vis.clear();
+      ray_visits_f32(v, o, u, near_t, far_t, cap, &vis);
+      bool have_prev = false;
+      double Dp = 0.0, tp = 0.0;
+      for (const auto& ii : vis) {
+        auto it = m.vox.find(VKey{ii[0], ii[1], ii[2]});
+        if (it == m.vox.end()) {
+          have_prev = false;
+          continue;
+        }
+        const Rec& r = it->second;
+        float e[3];
+        for (int a = 0; a < 3; ++a) {
+          float fi = (float)ii[a] + 0.5f;
+          float c = fi * v;
+          e[a] = c - o[a];
+        }
+        float t0 = e[0] * u[0];
+        float t1 = e[1] * u[1];
+        float t2 = e[2] * u[2];
+        float tc = t0 + t1;
+        tc = tc + t2;
+        if (have_prev && Dp > 0.0 && r.D <= 0.0) {
+          depth[pix] = tp + ((double)tc - tp) * Dp / (Dp - r.D);
+          for (int a = 0; a < 3; ++a) ijk[3 * pix + a] = ii[a];
+          if (P.mode != OPEN) {
+            int best = 0;
+            for (int c = 1; c < w; ++c)
+              if (r.sem[c] > r.sem[best]) best = c;
+            label[pix] = best;
+          } else if (q && sim) {
+            double dot = 0.0, mn = 0.0;
+            for (int c = 0; c < w; ++c) {
+              dot += r.sem[c] * (double)q[c];
+              mn += r.sem[c] * r.sem[c];
+            }
+            mn = std::sqrt(mn);
+            sim[pix] = (mn > 0.0 && qn > 0.0) ? dot / (mn * qn) : 0.0;
+          }
+          ++hits;
+          break;
+        }
+        have_prev = true;
+        Dp = r.D;
+        tp = (double)tc;
+      }
+    }
+  return hits;
+}
+
+// Voxels the render ray of one pixel enters (for pinning the traversal).
+int64_t ora_pixel_visits(float v, const double world_from_camera[16], float fx, float fy,
+                         float cx, float cy, int32_t px, int32_t py, float near_t, float far_t,
+                         int32_t* ijk, int64_t cap) {
+  float R[9], o[3], u[3];
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) R[a * 3 + b] = (float)world_from_camera[a * 4 + b];
+    o[a] = (float)world_from_camera[a * 4 + 3];
+  }
+  pixel_ray_f32(R, fx, fy, cx, cy, px, py, u);
+  std::vector<std::array<int32_t, 3>> vis;
+  const int vcap = 3 * (int)std::ceil(((double)far_t - (double)near_t) / (double)v) + 3;
+  ray_visits_f32(v, o, u, near_t, far_t, vcap, &vis);
+  int64_t k = 0;
+  for (auto& a : vis) {
+    if (k < cap)
+      for (int c = 0; c < 3; ++c) ijk[3 * k + c] = a[c];
+    ++k;
+  }
+  return k;
+}
+
 // Open-set read-out (end of Sec. III-D, Fig. "sit"): cosine similarity of each
 // voxel mean m (rows, n x l, FP64) against Q query embeddings (Q x l), softmax
 // over the queries of cos / temperature, most probable query, kept when its

@@ -549,3 +549,112 @@ def test_uncertainty_open_matches_scipy_student_t():
         scale = np.sqrt(ext["beta"][j] * (lam + 1.0) / (lam * nu))
         ref = st.t(df=2.0 * nu, loc=ext["sem"][j], scale=scale).var()
         np.testing.assert_allclose(unc[j], ref, rtol=1e-12)
+
+
+# ----------------------------------------------------------------- render
+def _cam_forward_x(o):
+    """world_from_camera: camera at o looking along +x (camera x -> world -y,
+    camera y -> world -z)."""
+    T = np.eye(4)
+    T[:3, :3] = np.array([[0.0, 0.0, 1.0], [-1.0, 0.0, 0.0], [0.0, -1.0, 0.0]])
+    T[:3, 3] = o
+    return T
+
+
+def test_render_traversal_brute_force():
+    """The render ray of a pixel enters exactly the cells its [near, far]
+    segment meets (seeded poses and pixels; near-grazing cells skipped)."""
+    rng = np.random.default_rng(11)
+    checked = 0
+    for _ in range(300):
+        pose = _rand_pose(rng, 0.4)
+        fx, fy, cx, cy = 60.0, 55.0, 32.0, 24.0
+        px, py = int(rng.integers(0, 64)), int(rng.integers(0, 48))
+        near, far = float(rng.uniform(0.0, 0.2)), float(rng.uniform(0.4, 0.9))
+        vis = oracle.pixel_visits(V, pose, fx, fy, cx, cy, px, py, near, far)
+        d = np.array([(px + 0.5 - cx) / fx, (py + 0.5 - cy) / fy, 1.0])
+        u = pose[:3, :3] @ (d / np.linalg.norm(d))
+        o = pose[:3, 3]
+        mid, half = 0.5 * (near + far), 0.5 * (far - near)
+        cells, amb = _segment_cells_fp64(o, o + mid * u, half, V, 1e-5)
+        if amb:
+            continue
+        got = [tuple(c) for c in vis.tolist()]
+        assert len(set(got)) == len(got)
+        assert set(got) == cells
+        assert (np.abs(np.diff(vis, axis=0)).sum(axis=1) == 1).all()
+        checked += 1
+    assert checked > 200
+
+
+def _plane_map(mode=oracle.CLOSED_ONEHOT, X0=2.0, dim=8, z=None):
+    """A map of the plane x = X0 observed from the origin: a 60 x 60 fan of
+    rays whose points lie on the plane (class 2 of 3, or embedding z)."""
+    v, tau = 0.05, 0.15
+    a = np.linspace(-0.4, 0.4, 60)
+    A, B = np.meshgrid(a, a, indexing="ij")
+    dirs = np.stack([np.ones_like(A), A, B], -1).reshape(-1, 3)
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    pts = (dirs * (X0 / dirs[:, 0])[:, None]).astype(np.float32)
+    if mode == oracle.OPEN:
+        m = oracle.OracleMap(voxel_size=v, trunc=tau, mode=mode, embed_dim=dim)
+        sem = np.tile(z, (len(pts), 1)).astype(np.float32)
+    else:
+        m = oracle.OracleMap(voxel_size=v, trunc=tau, mode=mode, num_classes=3)
+        sem = np.tile(np.array([0.1, 0.2, 0.7], np.float32), (len(pts), 1))
+    m.integrate(pts, np.eye(4), sem)
+    return m, v
+
+
+def test_render_plane_depth_closed_form():
+    """Rendering a plane x = X0 from the scan origin: every central pixel
+    hits, the depth is the ray distance to the plane X0 / u_x, and the label
+    is the plane's class. Depth error bound: a voxel is observed by scan rays
+    up to its angular half-size (sqrt(3) v / 2) / r away from the render ray,
+    over which the ray distance to the plane X0 / cos(theta) changes by
+    (sqrt(3) v / 2) tan(theta) at incidence angle theta (plus rounding)."""
+    X0 = 2.0
+    m, v = _plane_map(X0=X0)
+    W, H, f = 40, 30, 60.0
+    out = m.render(_cam_forward_x(np.zeros(3)), f, f, W / 2, H / 2, W, H, 0.3, 6.0)
+    d = np.stack(np.meshgrid((np.arange(W) + 0.5 - W / 2) / f, (np.arange(H) + 0.5 - H / 2) / f,
+                             indexing="xy"), -1)
+    ux = 1.0 / np.sqrt(1.0 + (d ** 2).sum(-1))  # world x component of the unit ray
+    true = X0 / ux
+    hit = np.isfinite(out["depth"])
+    assert hit[5:-5, 5:-5].all()
+    tan = np.sqrt(1.0 - ux ** 2) / ux
+    bound = np.sqrt(3.0) / 2.0 * v * tan + 0.01 * v
+    assert (np.abs(out["depth"] - true)[hit] <= bound[hit]).all()
+    assert (out["label"][hit] == 2).all()
+    assert (out["ijk"][hit][:, 0] * v <= X0 + v).all()
+
+
+def test_render_miss_and_behind():
+    """A camera looking away from the only surface sees nothing: depth +inf,
+    label -1, indices INT32_MIN."""
+    m, v = _plane_map()
+    T = _cam_forward_x(np.zeros(3))
+    T[:3, :3] = -T[:3, :3] @ np.diag([1.0, -1.0, 1.0])  # look along -x
+    out = m.render(T, 50.0, 50.0, 16, 12, 32, 24, 0.1, 6.0)
+    assert np.isinf(out["depth"]).all()
+    assert (out["label"] == -1).all()
+    assert (out["ijk"] == np.iinfo(np.int32).min).all()
+
+
+def test_render_open_similarity():
+    """Open set: the cosine of the hit voxel's mean with the query is 1 for
+    the observed embedding itself and 0 for an orthogonal query."""
+    z = np.zeros(8, np.float32)
+    z[3] = 2.0
+    m, v = _plane_map(mode=oracle.OPEN, z=z)
+    T = _cam_forward_x(np.zeros(3))
+    same = m.render(T, 50.0, 50.0, 16, 12, 32, 24, 0.3, 6.0, q=z)
+    hit = np.isfinite(same["depth"])
+    assert hit.sum() > 300
+    np.testing.assert_allclose(same["sim"][hit], 1.0, atol=1e-12)
+    q = np.zeros(8, np.float32)
+    q[5] = 1.0
+    orth = m.render(T, 50.0, 50.0, 16, 12, 32, 24, 0.3, 6.0, q=q)
+    np.testing.assert_allclose(orth["sim"][hit], 0.0, atol=1e-12)
+    assert (orth["label"] == -1).all()
