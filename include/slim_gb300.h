@@ -187,6 +187,30 @@ slim_status slim_extract_tsdf(slim_map* m, int32_t* ijk_dev, float* D_dev, float
                               float* sem_dev, float* beta_dev, int32_t* index_dev,
                               int64_t cap, int64_t* n_out, int32_t flags, void* stream);
 
+/* Ray-cast render of the map from a pinhole camera (Sec. III-E; the paper
+ * renders its VDB grid from a camera viewpoint with NanoVDB). Camera: x
+ * right, y down, looking along +z; pixel (px, py) looks along
+ * ((px + 0.5 - cx) / fx, (py + 0.5 - cy) / fy, 1), normalised, rotated by
+ * world_from_camera (row-major 4x4 FP64, rounded to FP32 like scan poses).
+ * Pixels are row-major, width x height (1..16384 each). Along each ray the
+ * voxels entered for t in [near_t, far_t] (0 <= near_t < far_t) are visited
+ * by the integration DDA; the surface is the first pair of consecutive
+ * visited voxels with positive weight and D_prev > 0 >= D, its depth the ray
+ * distance interpolated linearly between the two voxel-centre projections.
+ * Outputs (caller-owned device memory; all but depth_dev may be NULL):
+ *   depth_dev  float32 per pixel, +inf where no surface was found;
+ *   ijk_dev    int32 x 3 per pixel, the voxel after the crossing
+ *              (INT32_MIN where none);
+ *   label_dev  int32 per pixel: closed set, the largest count at that voxel
+ *              (ties to the lowest class); open set and misses, -1;
+ *   sim_dev    float32 per pixel: open set with q_dev (l float32, device):
+ *              cosine of the voxel's NIG mean with q; else 0.
+ * Asynchronous on `stream`. */
+slim_status slim_render(slim_map* m, const double world_from_camera[16], float fx, float fy,
+                        float cx, float cy, int32_t width, int32_t height, float near_t,
+                        float far_t, const float* q_dev, float* depth_dev, int32_t* ijk_dev,
+                        int32_t* label_dev, float* sim_dev, void* stream);
+
 /* Uncertainty read-out of the fused semantics, one row per allocated voxel
  * in the order of slim_extract_tsdf, same two-call protocol (cap == 0 writes
  * only *n_out). No counterpart in the paper's code; the quantities are the
@@ -296,7 +320,8 @@ typedef enum {
   SLIM_KERNEL_BACKWARD = 5,     /* adjoint gather */
   SLIM_KERNEL_BATCH = 6,        /* batched persistent integration */
   SLIM_KERNEL_RESET = 7,        /* slim_map_reset: re-zeroing of used closed-set blocks */
-  SLIM_KERNEL_KINDS = 8
+  SLIM_KERNEL_RENDER = 8,       /* slim_render ray casting */
+  SLIM_KERNEL_KINDS = 16
 } slim_kernel;
 
 /* Measurement aid (no counterpart in the paper). With on != 0 every kernel

@@ -552,6 +552,29 @@ slim_status slim_extract_tsdf(slim_map* m, int32_t* ijk_dev, float* D_dev, float
   return extract_impl(m, a, cap, n_out, (cudaStream_t)stream);
 }
 
+slim_status slim_render(slim_map* m, const double world_from_camera[16], float fx, float fy,
+                        float cx, float cy, int32_t width, int32_t height, float near_t,
+                        float far_t, const float* q_dev, float* depth_dev, int32_t* ijk_dev,
+                        int32_t* label_dev, float* sim_dev, void* stream) {
+  if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
+  if (!world_from_camera || !finite_pose(world_from_camera))
+    return fail(SLIM_ERR_ARG, "world_from_camera missing or not finite");
+  if (width < 1 || height < 1 || width > 16384 || height > 16384)
+    return fail(SLIM_ERR_ARG, "width and height must be in [1, 16384]");
+  if (!(fx > 0.f) || !(fy > 0.f) || !std::isfinite(fx) || !std::isfinite(fy) ||
+      !std::isfinite(cx) || !std::isfinite(cy))
+    return fail(SLIM_ERR_ARG, "fx, fy must be finite and > 0; cx, cy finite");
+  if (!(near_t >= 0.f) || !(far_t > near_t) || !std::isfinite(far_t))
+    return fail(SLIM_ERR_ARG, "need 0 <= near_t < far_t < inf");
+  if (((double)far_t - (double)near_t) / m->p.voxel_size > 1e6)
+    return fail(SLIM_ERR_ARG, "far_t - near_t spans more than 10^6 voxels");
+  if (!depth_dev) return fail(SLIM_ERR_ARG, "depth_dev is NULL");
+  if (sim_dev && m->mode == SLIM_OPEN && !q_dev)
+    return fail(SLIM_ERR_ARG, "sim_dev needs q_dev for an open-set map");
+  return run_render(m, world_from_camera, fx, fy, cx, cy, width, height, near_t, far_t, q_dev,
+                    depth_dev, ijk_dev, label_dev, sim_dev, (cudaStream_t)stream);
+}
+
 slim_status slim_extract_uncertainty(slim_map* m, float* unc_dev, int64_t cap, int64_t* n_out,
                                      void* stream) {
   if (!m || !n_out) return fail(SLIM_ERR_ARG, "map or n_out is NULL");

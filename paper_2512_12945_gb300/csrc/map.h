@@ -101,6 +101,10 @@ void prof_end(slim_map* m, int token, cudaStream_t st);
 slim_status open_alloc_scratch(slim_map* m, OpenScratch& o, int64_t max_points);
 cudaError_t open_setup_attributes(slim_map* m);
 cudaError_t query_setup_attributes();
+slim_status run_render(slim_map* m, const double world_from_camera[16], float fx, float fy,
+                       float cx, float cy, int32_t width, int32_t height, float near_t,
+                       float far_t, const float* q, float* depth, int32_t* ijk, int32_t* label,
+                       float* sim, cudaStream_t st);
 slim_status run_backward(slim_map* m, const ScanGeom& g, const float* pts, const float* sem,
                          int64_t n, const float* gD, const float* gS, const float* gB,
                          float* gsem, float* gxyz, cudaStream_t st);

@@ -60,9 +60,10 @@ EXPORTS = ["slim_map_params_default", "slim_map_create", "slim_map_destroy", "sl
            "slim_integrate", "slim_integrate_host", "slim_map_sync", "slim_map_stats",
            "slim_extract_tsdf", "slim_query", "slim_backward", "slim_integrate_batch",
            "slim_profile_enable", "slim_profile_read", "slim_autotune", "slim_query_rows_static",
-           "slim_extract_uncertainty", "slim_last_error"]
+           "slim_extract_uncertainty", "slim_render", "slim_last_error"]
 KERNELS = ["traverse", "fuse_closed", "open_pairs", "open_apply", "query", "backward", "batch",
-           "reset"]
+           "reset", "render"]
+N_KINDS = 16
 
 _lock = threading.Lock()
 _lib = None
@@ -102,6 +103,7 @@ def lib():
             "slim_autotune": [P, P, I64, P, P, P, ctypes.POINTER(I32)],
             "slim_query_rows_static": [P, I64, I32, P, I32, F, F, P, P, P],
             "slim_extract_uncertainty": [P, P, I64, ctypes.POINTER(I64), P],
+            "slim_render": [P, P, F, F, F, F, I32, I32, F, F, P, P, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -235,6 +237,30 @@ def slim_extract_uncertainty(h, mode, width, stream=None, device=None):
     return unc
 
 
+def slim_render(h, world_from_camera, fx, fy, cx, cy, width, height, near, far, q=None,
+                stream=None, device=None):
+    """Ray-cast render: dict of depth (H, W) float32 (+inf on a miss), ijk
+    (H, W, 3) int32, label (H, W) int32 and, with a query q (open set,
+    float32 l-vector on the device), sim (H, W) float32."""
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    depth = torch.empty((height, width), dtype=torch.float32, device=dev)
+    ijk = torch.empty((height, width, 3), dtype=torch.int32, device=dev)
+    label = torch.empty((height, width), dtype=torch.int32, device=dev)
+    sim = torch.empty((height, width), dtype=torch.float32, device=dev) if q is not None else None
+    keep, p_pose = _pose_arr(world_from_camera)
+    qp = None if q is None else _dev_ptr(q, torch.float32, "q")
+    _check(lib().slim_render(h, p_pose, float(fx), float(fy), float(cx), float(cy), int(width),
+                             int(height), float(near), float(far), qp,
+                             ctypes.c_void_p(depth.data_ptr()), ctypes.c_void_p(ijk.data_ptr()),
+                             ctypes.c_void_p(label.data_ptr()),
+                             None if sim is None else ctypes.c_void_p(sim.data_ptr()),
+                             _stream(stream)), "slim_render")
+    out = dict(depth=depth, ijk=ijk, label=label)
+    if sim is not None:
+        out["sim"] = sim
+    return out
+
+
 def slim_query(h, q_bf16, temperature, tp, n_rows, scores=False, stream=None):
     q = q_bf16
     if q.dtype != torch.bfloat16:
@@ -295,8 +321,8 @@ def slim_profile_enable(h, on):
 
 def slim_profile_read(h):
     """{kernel name: (launches, total ms)} since the last read."""
-    n = (ctypes.c_int64 * 8)()
-    ms = (ctypes.c_double * 8)()
+    n = (ctypes.c_int64 * N_KINDS)()
+    ms = (ctypes.c_double * N_KINDS)()
     _check(lib().slim_profile_read(h, n, ms), "slim_profile_read")
     return {KERNELS[k]: (int(n[k]), float(ms[k])) for k in range(len(KERNELS)) if n[k]}
 
@@ -387,6 +413,11 @@ class Map:
 
     def extract(self, posterior=False, index=False, stream=None):
         return slim_extract_tsdf(self.handle, self.mode, self.width, posterior, index, stream)
+
+    def render(self, world_from_camera, fx, fy, cx, cy, width, height, near, far, q=None,
+               stream=None):
+        return slim_render(self.handle, world_from_camera, fx, fy, cx, cy, width, height, near,
+                           far, q, stream)
 
     def uncertainty(self, stream=None):
         return slim_extract_uncertainty(self.handle, self.mode, self.width, stream)
