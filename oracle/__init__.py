@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CLOSED_ONEHOT, CLOSED_SOFT, OPEN = 0, 1, 2
+CLOSED_ONEHOT, CLOSED_SOFT, OPEN, CLOSED_LATEST = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:

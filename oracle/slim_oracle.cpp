@@ -6,7 +6,8 @@
 //     weighted running average of the truncated signed distance (equation for
 //     D_t and Eq. (Wx) for W_t, with the weighting function w~ = 1).
 //   * Sec. III-C "Closed-Set Semantic Fusion": Theorem 1 / Eq. (alpha_update)
-//     Dirichlet count update, Eq. (dir_to_cat) posterior predictive.
+//     Dirichlet count update, Eq. (dir_to_cat) posterior predictive; and the
+//     non-Bayesian ablation of Sec. IV (SLIM-VDB*): the latest label wins.
 //   * Sec. III-D "Open-Set Semantic Fusion": Theorem 2 / Eqs. (norm_update_1)
 //     to (norm_update_4) Normal-Inverse-Gamma update, with the implementation
 //     simplification stated at the end of Sec. III-D (lambda = 2 nu = W, only
@@ -41,7 +42,7 @@
 
 namespace {
 
-enum Mode : int32_t { CLOSED_ONEHOT = 0, CLOSED_SOFT = 1, OPEN = 2 };
+enum Mode : int32_t { CLOSED_ONEHOT = 0, CLOSED_SOFT = 1, OPEN = 2, CLOSED_LATEST = 3 };
 
 struct Params {
   float voxel_size;
@@ -318,6 +319,11 @@ void fuse(const Params& P, Rec& rec, double d, const float* s) {
   } else if (P.mode == CLOSED_SOFT) {
     // Soft-count reading of Eq. (alpha_update): alpha_i += p_i.
     for (int k = 0; k < P.num_classes; ++k) rec.sem[k] += (double)s[k];
+  } else if (P.mode == CLOSED_LATEST) {
+    // The non-Bayesian ablation of the evaluation (SLIM-VDB*): the voxel
+    // keeps the most recent measurement's label, as a one-hot vector.
+    std::fill(rec.sem.begin(), rec.sem.end(), 0.0);
+    rec.sem[argmax_first(s, P.num_classes)] = 1.0;
   } else {
     // Theorem 2 with |Z| = 1 and lambda = W_prev (Sec. III-D):
     //   m~ = (lambda m + z) / (lambda + 1)
@@ -456,7 +462,7 @@ int64_t ora_extract(void* h, int32_t* ijk, double* D, double* W, double* sem, do
     if (D) D[j] = r.D;
     if (W) W[j] = r.W;
     if (sem) {
-      if (P.mode != OPEN && posterior) {
+      if (P.mode != OPEN && P.mode != CLOSED_LATEST && posterior) {
         // Eq. (dir_to_cat): p(z = i) = alpha~_i / sum_j alpha~_j, with
         // alpha~_i = alpha0 + c_i.
         double tot = 0.0;

@@ -658,3 +658,34 @@ def test_render_open_similarity():
     orth = m.render(T, 50.0, 50.0, 16, 12, 32, 24, 0.3, 6.0, q=q)
     np.testing.assert_allclose(orth["sim"][hit], 0.0, atol=1e-12)
     assert (orth["label"] == -1).all()
+
+
+def test_latest_label_mode_is_last_writer():
+    """SLIM-VDB* (latest measurement wins): the label each voxel keeps is the
+    argmax of the last observation in scan, then point, then ray order,
+    replayed from the pair list; D and W are those of the Bayesian modes."""
+    w = synth.room_lidar(seed=1, n_scans=3, K=10)
+    kw = dict(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=10, min_range=w.min_range,
+              max_range=w.max_range)
+    lat = oracle.OracleMap(mode=oracle.CLOSED_LATEST, **kw)
+    hot = oracle.OracleMap(mode=oracle.CLOSED_ONEHOT, **kw)
+    p = oracle.make_params(w.voxel_size, w.trunc, mode=oracle.CLOSED_LATEST, num_classes=10,
+                           min_range=w.min_range, max_range=w.max_range)
+    last = {}
+    for s in w.scans:
+        lat.integrate(s["pts"], s["pose"], s["sem"])
+        hot.integrate(s["pts"], s["pose"], s["sem"])
+        ijk, pt, _ = oracle.scan_pairs(p, s["pts"], s["pose"])
+        lab = np.argmax(s["sem"], axis=1)
+        for k, j in zip(map(tuple, ijk.tolist()), pt.tolist()):
+            last[k] = lab[j]
+    e, h = lat.extract(), hot.extract()
+    assert np.array_equal(e["ijk"], h["ijk"])
+    np.testing.assert_array_equal(e["W"], h["W"])
+    np.testing.assert_allclose(e["D"], h["D"], rtol=0, atol=0)
+    assert np.all(e["sem"].sum(1) == 1.0)
+    got = np.argmax(e["sem"], axis=1)
+    want = np.array([last[tuple(k)] for k in e["ijk"].tolist()])
+    assert np.array_equal(got, want)
+    # the ablation differs from the Bayesian counts wherever labels disagree
+    assert (got != np.argmax(h["sem"], axis=1)).any()
