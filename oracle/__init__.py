@@ -74,6 +74,9 @@ def _load():
             lib.ora_uncertainty.restype = ctypes.c_int64
             lib.ora_uncertainty.argtypes = [P, P]
             F = ctypes.c_float
+            lib.ora_integrate_depth.restype = ctypes.c_int64
+            lib.ora_integrate_depth.argtypes = [P, P, ctypes.c_int32, ctypes.c_int32, F, F, F, F,
+                                                P, P]
             lib.ora_render.restype = ctypes.c_int64
             lib.ora_render.argtypes = [P, P, F, F, F, F, ctypes.c_int32, ctypes.c_int32, F, F,
                                        P, P, P, P, P]
@@ -147,6 +150,16 @@ class OracleMap:
         assert sem.shape[0] == pts.shape[0]
         pose = _pose(pose)
         return self.lib.ora_integrate(self.h, _ptr(pts), pts.shape[0], _ptr(pose), _ptr(sem))
+
+    def integrate_depth(self, depth, fx, fy, cx, cy, pose, sem):
+        """One row-major z-depth image (H, W) float32 with per-pixel semantics
+        (H*W, w); returns the number of valid points."""
+        depth = np.ascontiguousarray(depth, np.float32)
+        h, w = depth.shape
+        sem = _f32(sem, self.w)
+        assert sem.shape[0] == h * w
+        return self.lib.ora_integrate_depth(self.h, _ptr(depth), w, h, fx, fy, cx, cy,
+                                            _ptr(_pose(pose)), _ptr(sem))
 
     def count(self):
         return self.lib.ora_count(self.h)

@@ -395,6 +395,37 @@ int64_t ora_integrate(void* h, const float* pts, int64_t n, const double pose[16
   return valid;
 }
 
+// Integrate one depth frame (the RGB-D front end): pixel (u, v) of a
+// row-major width x height z-depth image (metres along the camera's optical
+// axis) back-projects, in FP32 with this op order, to the sensor-frame point
+// p = (((u + 0.5) - cx) / fx * z, ((v + 0.5) - cy) / fy * z, z); pixels with
+// a non-finite or non-positive z are invalid. The points then go through
+// ora_integrate unchanged (sem: one row per pixel). Returns the number of
+// valid points.
+int64_t ora_integrate_depth(void* h, const float* depth, int32_t width, int32_t height, float fx,
+                            float fy, float cx, float cy, const double pose[16],
+                            const float* sem) {
+  const int64_t n = (int64_t)width * height;
+  std::vector<float> pts((size_t)n * 3);
+  for (int32_t v = 0; v < height; ++v)
+    for (int32_t u = 0; u < width; ++u) {
+      const int64_t j = (int64_t)v * width + u;
+      const float z = depth[j];
+      if (!(z > 0.0f) || !std::isfinite(z)) {
+        pts[3 * j + 0] = pts[3 * j + 1] = pts[3 * j + 2] = NAN;
+        continue;
+      }
+      float au = (float)u + 0.5f;
+      float av = (float)v + 0.5f;
+      float xu = (au - cx) / fx;
+      float yv = (av - cy) / fy;
+      pts[3 * j + 0] = xu * z;
+      pts[3 * j + 1] = yv * z;
+      pts[3 * j + 2] = z;
+    }
+  return ora_integrate(h, pts.data(), n, pose, sem);
+}
+
 // All (voxel, point) observations of one scan, in point then ray order.
 // Returns the number of pairs (or the required count when cap is too small).
 int64_t ora_scan_pairs(const ora_params* p, const float* pts, int64_t n, const double pose[16],

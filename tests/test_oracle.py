@@ -689,3 +689,44 @@ def test_latest_label_mode_is_last_writer():
     assert np.array_equal(got, want)
     # the ablation differs from the Bayesian counts wherever labels disagree
     assert (got != np.argmax(h["sem"], axis=1)).any()
+
+
+def test_integrate_depth_backprojection():
+    """RGB-D front end: integrating a z-depth image equals integrating the
+    points back-projected in FP32 as ((u + 0.5 - cx) / fx * z, ...,  z) (numpy
+    float32, same op order), bit for bit; invalid depths are skipped; the
+    principal-point pixel back-projects onto the optical axis."""
+    w = synth.indoor_rgbd(seed=3, n_frames=40, width=64, height=48, dim=16, frames=[2])
+    s = w.scans[0]
+    H, W_ = 48, 64
+    f = np.float32(525.0 * W_ / 640.0)
+    cx, cy = np.float32(W_ / 2), np.float32(H / 2)
+    depth = s["pts"][:, 2].reshape(H, W_).astype(np.float32).copy()
+    depth[0, :5] = np.nan
+    depth[1, :5] = -1.0
+    u = np.arange(W_, dtype=np.float32)[None, :] + np.float32(0.5)
+    v = np.arange(H, dtype=np.float32)[:, None] + np.float32(0.5)
+    xu = ((u - cx) / f).astype(np.float32)
+    yv = ((v - cy) / f).astype(np.float32)
+    pts = np.stack([np.broadcast_to(xu, (H, W_)) * depth, np.broadcast_to(yv, (H, W_)) * depth,
+                    depth], -1).reshape(-1, 3).astype(np.float32)
+    pts[~(np.isfinite(depth) & (depth > 0)).reshape(-1)] = np.nan  # invalid pixels
+    kw = dict(voxel_size=w.voxel_size, trunc=w.trunc, mode=oracle.OPEN, embed_dim=16,
+              min_range=w.min_range, max_range=w.max_range)
+    a, b = oracle.OracleMap(**kw), oracle.OracleMap(**kw)
+    na = a.integrate_depth(depth, f, f, cx, cy, s["pose"], s["sem"])
+    nb = b.integrate(pts, s["pose"], s["sem"])
+    assert na == nb and na < H * W_ - 9
+    ea, eb = a.extract(), b.extract()
+    for k in ("ijk", "W", "D", "sem", "beta"):
+        assert np.array_equal(ea[k], eb[k]), k
+    # one valid pixel at the principal point: a ray along the optical axis
+    one = np.zeros((2, 2), np.float32)
+    one[1, 1] = 1.0
+    c = oracle.OracleMap(voxel_size=0.1, trunc=0.3, mode=oracle.CLOSED_ONEHOT, num_classes=2,
+                         min_range=0.1, max_range=10.0)
+    c.integrate_depth(one, 1.0, 1.0, 1.5, 1.5, np.eye(4), np.full((4, 2), 0.5, np.float32))
+    e = c.extract()
+    assert len(e["W"]) > 0 and (e["ijk"][:, :2] == 0).all()
+    np.testing.assert_allclose(e["D"], np.clip(1.0 - (e["ijk"][:, 2] + 0.5) * 0.1, -0.3, 0.3),
+                               atol=1e-6)
