@@ -596,6 +596,9 @@ def run_indoor(args):
     pts = [torch.from_numpy(s["pts"]).cuda() for s in w.scans]
     sem = [torch.from_numpy(s["sem"]).cuda() for s in w.scans]
     valid = sum(int((np.linalg.norm(s["pts"], axis=1) >= w.min_range).sum()) for s in w.scans)
+    fpx = 525.0
+    depths = [torch.from_numpy(np.ascontiguousarray(s["pts"][:, 2].reshape(480, 640),
+                                                    np.float32)).cuda() for s in w.scans]
     stream = torch.cuda.current_stream()
     out = {}
     for storage in ("f32", "bf16"):
@@ -609,6 +612,14 @@ def run_indoor(args):
             for p, q, s in zip(pts, sem, w.scans):
                 m.integrate(p, s["pose"], q)
 
+        def step_depth():  # the same frames as z-depth images (RGB-D front end)
+            m.reset()
+            for dimg, q, s in zip(depths, sem, w.scans):
+                m.integrate_depth(dimg, fpx, fpx, 320.0, 240.0, s["pose"], q)
+
+        for _ in range(args.warmup):
+            step_depth()
+        dms = _timed(step_depth, args.steps, 0, stream)
         for _ in range(args.warmup):
             step()
         slim.slim_profile_enable(m.handle, True)
@@ -630,6 +641,9 @@ def run_indoor(args):
         peak, kind = _bf16_peak()
         out[storage] = {"points_per_s": valid * args.steps / (ms * args.steps / 1e3),
                         "ms_per_step": ms, "voxels": rows,
+                        "depth_front_end": {"ms_per_step": dms,
+                                            "points_per_s": valid / (dms / 1e3),
+                                            "call": "slim_integrate_depth per frame"},
                         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
                         "query": {"ms": qms, "kernel_ms": kq, "tflops": flops / (kq / 1e3) / 1e12,
                                   "roofline": {"bound": "tensor", "peak": peak, "unit": "TFLOP/s",

@@ -59,7 +59,13 @@ typedef enum {
   SLIM_CLOSED_SOFT = 1,
   /* Theorem 2 / Eqs. (norm_update_1)-(norm_update_4) with lambda = 2 nu = W
    * (Sec. III-D): per-element NIG mean m and beta of l-dim embeddings. */
-  SLIM_OPEN = 2
+  SLIM_OPEN = 2,
+  /* The non-Bayesian ablation of the evaluation (SLIM-VDB*, Sec. IV): the
+   * voxel keeps the label (argmax) of its most recent observation — last in
+   * scan, then point-index order; D and W as in the other modes. Direct
+   * reductions only; extract writes the label as a one-hot row; no
+   * uncertainty read-out, no adjoint. */
+  SLIM_CLOSED_LATEST = 3
 } slim_mode;
 
 typedef enum { SLIM_STORE_F32 = 0, SLIM_STORE_BF16 = 1 } slim_storage;
@@ -150,6 +156,20 @@ slim_status slim_map_reset(slim_map* m, void* stream);
 slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
                            const double pose_host[16], const void* sem_dev,
                            void* stream);
+
+/* RGB-D front end (no counterpart in the paper's code, which back-projects
+ * depth frames on the CPU): integrate one row-major width x height z-depth
+ * image (float32 metres along the optical axis, device memory) without
+ * materialising points. Pixel (u, v) is the sensor-frame point
+ * (((u + 0.5) - cx) / fx * z, ((v + 0.5) - cy) / fy * z, z), computed in
+ * this FP32 op order inside the traversal kernels; non-finite or
+ * non-positive depths are invalid; then everything is as in slim_integrate
+ * (sem_dev: one row per pixel, width * height <= max_points). One-hot and
+ * latest-label maps use the direct kernel, soft counts the sort tiles, the
+ * open set its usual pipeline. Asynchronous on `stream`. */
+slim_status slim_integrate_depth(slim_map* m, const float* depth_dev, int32_t width,
+                                 int32_t height, float fx, float fy, float cx, float cy,
+                                 const double pose_host[16], const void* sem_dev, void* stream);
 
 /* As slim_integrate with pts_host / sem_host in host memory: the library
  * copies them into its own device staging buffers on `stream` (pinned host

@@ -87,6 +87,11 @@ void compose_pose(const double pose[16], const double ext[16], ScanGeom& g, floa
   volatile float lim = 524288.0f * v;  // float product, as in the geometry spec
   g.lim = lim;
   g.cap = cap;
+  g.scan_no = 0;
+  g.depth = nullptr;
+  g.dw = 0;
+  g.fx = g.fy = 1.f;
+  g.cx = g.cy = 0.f;
 }
 
 bool finite_pose(const double* p) {
@@ -119,7 +124,7 @@ slim_status check_params(const slim_map_params* p) {
     return fail(SLIM_ERR_ARG, "trunc must be in (0, 4 * voxel_size]");
   if (!(p->min_range >= 0.f) || !(p->max_range > p->min_range))
     return fail(SLIM_ERR_ARG, "need 0 <= min_range < max_range");
-  if (p->mode < 0 || p->mode > 2) return fail(SLIM_ERR_ARG, "mode must be 0, 1 or 2");
+  if (p->mode < 0 || p->mode > 3) return fail(SLIM_ERR_ARG, "mode must be 0, 1, 2 or 3");
   if (p->mode != SLIM_OPEN && (p->num_classes < 1 || p->num_classes > 64))
     return fail(SLIM_ERR_ARG, "num_classes must be in [1, 64]");
   if (p->mode == SLIM_OPEN) {
@@ -144,9 +149,14 @@ slim_status check_params(const slim_map_params* p) {
     return fail(SLIM_ERR_ARG, "tile_points must be 0 (default), 64, 128 or 256");
   if (p->aggregation < 0 || p->aggregation > 3)
     return fail(SLIM_ERR_ARG, "aggregation must be 0 (auto), 1 (sort), 2 (hash) or 3 (direct)");
-  if ((p->aggregation == SLIM_AGG_HASH || p->aggregation == SLIM_AGG_DIRECT) &&
-      p->mode != SLIM_CLOSED_ONEHOT)
-    return fail(SLIM_ERR_ARG, "hash and direct aggregation serve the closed one-hot mode only");
+  if (p->aggregation == SLIM_AGG_HASH && p->mode != SLIM_CLOSED_ONEHOT)
+    return fail(SLIM_ERR_ARG, "hash aggregation serves the closed one-hot mode only");
+  if (p->aggregation == SLIM_AGG_DIRECT && p->mode != SLIM_CLOSED_ONEHOT &&
+      p->mode != SLIM_CLOSED_LATEST)
+    return fail(SLIM_ERR_ARG, "direct aggregation serves the one-hot and latest-label modes");
+  if (p->mode == SLIM_CLOSED_LATEST && p->aggregation != SLIM_AGG_AUTO &&
+      p->aggregation != SLIM_AGG_DIRECT)
+    return fail(SLIM_ERR_ARG, "the latest-label mode uses direct reductions only");
   return SLIM_OK;
 }
 
@@ -189,7 +199,11 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   m->L = p->mode == SLIM_OPEN ? p->embed_dim : 0;
   m->bf16 = (p->mode == SLIM_OPEN && p->embed_storage == SLIM_STORE_BF16) ? 1 : 0;
   // one-hot records keep (S_k, c_k) per class, soft records (S, W, c_k)
-  m->rs = p->mode == SLIM_CLOSED_ONEHOT ? (2 * m->K + 3) / 4 * 4 : ((2 + m->K) + 3) / 4 * 4;
+  // record floats: one-hot {S_k, c_k} per class; soft {S, W, c_k}; latest
+  // {S, W, stamp (u64)}
+  m->rs = p->mode == SLIM_CLOSED_ONEHOT  ? (2 * m->K + 3) / 4 * 4
+          : p->mode == SLIM_CLOSED_LATEST ? 4
+                                          : ((2 + m->K) + 3) / 4 * 4;
   const double q = 2.0 * (double)p->trunc / (double)p->voxel_size;
   m->cap = 3 * (int)std::ceil(q) + 3;
   const int span = (int)std::ceil(q) + 2;
@@ -201,9 +215,10 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   }
   m->tile_points = closed_tile_points(m->cap, m->band_blocks);
   m->hash_tile = p->tile_points > 0 ? p->tile_points : 256;
-  m->direct = p->mode == SLIM_CLOSED_ONEHOT &&
-              (p->aggregation == SLIM_AGG_DIRECT ||
-               (p->aggregation == SLIM_AGG_AUTO && p->tile_points == 0));
+  m->direct = p->mode == SLIM_CLOSED_LATEST ||
+              (p->mode == SLIM_CLOSED_ONEHOT &&
+               (p->aggregation == SLIM_AGG_DIRECT ||
+                (p->aggregation == SLIM_AGG_AUTO && p->tile_points == 0)));
   m->n_entries = next_pow2((uint64_t)p->hash_capacity);
   const uint64_t nh = m->n_entries;
   const uint64_t bc = (uint64_t)p->block_capacity;
@@ -295,7 +310,7 @@ slim_status slim_map_destroy(slim_map* m) {
 
 // Closed one-hot map integrated by direct per-pair reductions.
 static bool uses_direct(const slim_map* m) {
-  return m->mode == SLIM_CLOSED_ONEHOT && m->direct;
+  return (m->mode == SLIM_CLOSED_ONEHOT || m->mode == SLIM_CLOSED_LATEST) && m->direct;
 }
 
 // Closed one-hot map integrated by the shared-memory hash tiles.
@@ -334,12 +349,14 @@ slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
   compose_pose(pose_host, m->p.body_from_sensor, g, m->p.voxel_size, m->p.trunc,
                m->p.min_range, m->p.max_range, m->cap);
   m->scans++;
+  g.scan_no = (uint32_t)m->scans;
   if (n == 0) return SLIM_OK;
   const float* sem = static_cast<const float*>(sem_dev);
   if (m->mode != SLIM_OPEN) {
     const int tok = prof_begin(m, SLIM_KERNEL_FUSE_CLOSED, st);
     if (uses_direct(m))
-      SLIM_CUDA(launch_fuse_direct(m->mv, g, pts_dev, sem, n, m->K, st));
+      SLIM_CUDA(launch_fuse_direct(m->mv, g, pts_dev, sem, n, m->K,
+                                   m->mode == SLIM_CLOSED_LATEST ? 1 : 0, st));
     else if (uses_hash(m))
       SLIM_CUDA(launch_fuse_hash(m->mv, g, pts_dev, sem, n, m->K, m->hash_tile, m->band_blocks,
                                  st));
@@ -352,6 +369,53 @@ slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
   SLIM_CUDA(launch_traverse_alloc(m->mv, g, pts_dev, n, true, st));
   prof_end(m, tok, st);
   return open_integrate(m, m->mv, m->open, g, pts_dev, sem, n, m->L, m->bf16, st);
+}
+
+slim_status slim_integrate_depth(slim_map* m, const float* depth_dev, int32_t width,
+                                 int32_t height, float fx, float fy, float cx, float cy,
+                                 const double pose_host[16], const void* sem_dev, void* stream) {
+  if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
+  if (width < 1 || height < 1) return fail(SLIM_ERR_ARG, "width and height must be >= 1");
+  const int64_t n = (int64_t)width * height;
+  if (n > m->p.max_points) return fail(SLIM_ERR_ARG, "width * height must be <= max_points");
+  if (!pose_host || !finite_pose(pose_host)) return fail(SLIM_ERR_ARG, "pose missing or not finite");
+  if (!(fx > 0.f) || !(fy > 0.f) || !std::isfinite(fx) || !std::isfinite(fy) ||
+      !std::isfinite(cx) || !std::isfinite(cy))
+    return fail(SLIM_ERR_ARG, "fx, fy must be finite and > 0; cx, cy finite");
+  if (!depth_dev || !sem_dev) return fail(SLIM_ERR_ARG, "depth/sem NULL");
+  if ((reinterpret_cast<uintptr_t>(depth_dev) & 3) || (reinterpret_cast<uintptr_t>(sem_dev) & 3))
+    return fail(SLIM_ERR_ARG, "depth/sem must be 4-byte aligned");
+  if (m->mode == SLIM_OPEN && (reinterpret_cast<uintptr_t>(sem_dev) & 15))
+    return fail(SLIM_ERR_ARG, "open-set embeddings must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  ScanGeom g;
+  compose_pose(pose_host, m->p.body_from_sensor, g, m->p.voxel_size, m->p.trunc,
+               m->p.min_range, m->p.max_range, m->cap);
+  m->scans++;
+  g.scan_no = (uint32_t)m->scans;
+  g.depth = depth_dev;
+  g.dw = width;
+  g.fx = fx;
+  g.fy = fy;
+  g.cx = cx;
+  g.cy = cy;
+  const float* sem = static_cast<const float*>(sem_dev);
+  if (m->mode != SLIM_OPEN) {
+    // one-hot and latest maps take the direct kernel (the hash tiles read
+    // point arrays); soft counts the sort tiles
+    const int tok = prof_begin(m, SLIM_KERNEL_FUSE_CLOSED, st);
+    if (m->mode == SLIM_CLOSED_SOFT)
+      SLIM_CUDA(launch_fuse_closed(m->mv, g, nullptr, sem, n, m->mode, m->K, m->tile_points, st));
+    else
+      SLIM_CUDA(launch_fuse_direct(m->mv, g, nullptr, sem, n, m->K,
+                                   m->mode == SLIM_CLOSED_LATEST ? 1 : 0, st));
+    prof_end(m, tok, st);
+    return SLIM_OK;
+  }
+  const int tok = prof_begin(m, SLIM_KERNEL_TRAVERSE, st);
+  SLIM_CUDA(launch_traverse_alloc(m->mv, g, nullptr, n, true, st));
+  prof_end(m, tok, st);
+  return open_integrate(m, m->mv, m->open, g, nullptr, sem, n, m->L, m->bf16, st);
 }
 
 slim_status slim_integrate_host(slim_map* m, const float* pts_host, int64_t n,
@@ -405,6 +469,8 @@ slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
     b.job[k].n = n;
     b.job[k].K = m->K;
     b.job[k].band_blocks = m->band_blocks;
+    b.job[k].latest = 0;
+    b.job[k].g.scan_no = 1;
   }
   const bool prof = m->prof_on;
   m->prof_on = false;
@@ -580,6 +646,8 @@ slim_status slim_extract_uncertainty(slim_map* m, float* unc_dev, int64_t cap, i
   if (!m || !n_out) return fail(SLIM_ERR_ARG, "map or n_out is NULL");
   if (cap < 0) return fail(SLIM_ERR_ARG, "cap must be >= 0");
   if (cap > 0 && !unc_dev) return fail(SLIM_ERR_ARG, "unc_dev is NULL");
+  if (m->mode == SLIM_CLOSED_LATEST)
+    return fail(SLIM_ERR_UNSUPPORTED, "the latest-label mode keeps no distribution");
   ExtractArgs a{};
   a.unc = unc_dev;
   return extract_impl(m, a, cap, n_out, (cudaStream_t)stream);
@@ -617,6 +685,8 @@ slim_status slim_backward(slim_map* m, const float* pts_dev, int64_t n,
   if (!pose_host || !finite_pose(pose_host)) return fail(SLIM_ERR_ARG, "pose missing or not finite");
   if (n > 0 && (!pts_dev || !sem_dev || !gD_dev || !gsem_dev || !gxyz_dev))
     return fail(SLIM_ERR_ARG, "pts, sem, gD, gsem and gxyz are required");
+  if (m->mode == SLIM_CLOSED_LATEST)
+    return fail(SLIM_ERR_UNSUPPORTED, "the latest-label mode has no adjoint");
   if (n > 0 && m->mode != SLIM_CLOSED_ONEHOT && !gS_dev)
     return fail(SLIM_ERR_ARG, "gS is required in the soft and open modes");
   ScanGeom g;
@@ -684,12 +754,14 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
       HashJob& J = nb.job[nb.n_jobs++];
       compose_pose(it.pose, m->p.body_from_sensor, J.g, m->p.voxel_size, m->p.trunc,
                    m->p.min_range, m->p.max_range, m->cap);
+      J.g.scan_no = (uint32_t)m->scans;
       J.mv = m->mv;
       J.pts = it.pts_dev;
       J.sem = static_cast<const float*>(it.sem_dev);
       J.n = it.n;
       J.K = m->K;
       J.band_blocks = m->band_blocks;
+      J.latest = m->mode == SLIM_CLOSED_LATEST ? 1 : 0;
       if (nb.n_jobs == kMaxHashJobs) {
         slim_status s = flush_direct();
         if (s != SLIM_OK) return s;
@@ -702,6 +774,8 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
       HashJob& J = b.job[b.n_jobs++];
       compose_pose(it.pose, m->p.body_from_sensor, J.g, m->p.voxel_size, m->p.trunc,
                    m->p.min_range, m->p.max_range, m->cap);
+      J.g.scan_no = (uint32_t)m->scans;
+      J.latest = 0;
       J.mv = m->mv;
       J.pts = it.pts_dev;
       J.sem = static_cast<const float*>(it.sem_dev);

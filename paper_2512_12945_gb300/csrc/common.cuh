@@ -69,6 +69,12 @@ struct ScanGeom {
   float rmin, rmax;
   float lim;    // |coordinate| bound: 2^19 voxels
   int32_t cap;  // DDA step cap: 3 * ceil(2 tau / v) + 3
+  uint32_t scan_no;  // the map's scan count at this scan (latest-label stamps)
+  // depth front end: when depth is set, point j is back-projected from the
+  // row-major z-depth image (dw pixels per row) instead of read from pts
+  const float* depth;
+  int32_t dw;
+  float fx, fy, cx, cy;
 };
 
 // Block key: each block coordinate offset by 2^20 into 21 bits, x highest,

@@ -78,7 +78,17 @@ __global__ void __launch_bounds__(256) k_extract_write(MapView mv, const uint32_
       a.ijk[3 * o + 1] = by * 8 + ((l >> 3) & 7);
       a.ijk[3 * o + 2] = bz * 8 + (l & 7);
     }
-    if (!open) {
+    if (!open && a.mode == SLIM_CLOSED_LATEST) {
+      // {S, W, stamp}: the label is the stamp's low byte
+      const float* r = mv.rec + ((size_t)slot * kBlockVoxels + l) * mv.rs;
+      if (a.D) a.D[o] = r[0] / r[1];
+      if (a.W) a.W[o] = r[1];
+      if (a.index) a.index[o] = (int32_t)(slot * kBlockVoxels + l);
+      if (a.sem) {
+        const uint32_t lab = (uint32_t)(*reinterpret_cast<const unsigned long long*>(r + 2) & 0xFF);
+        for (int k = 0; k < a.K; ++k) a.sem[o * a.K + k] = k == (int)lab ? 1.f : 0.f;
+      }
+    } else if (!open) {
       const float* r = mv.rec + ((size_t)slot * kBlockVoxels + l) * mv.rs;
       // one-hot records hold (S_k, c_k) pairs, soft records (S, W, c_k)
       const float* cnt = mv.split ? r + 1 : r + 2;

@@ -18,6 +18,11 @@
 //
 // One kernel serves a single scan and a batch of scans of many maps (the
 // HashBatch job table): each CTA takes 256 points of one job.
+//
+// Latest-label maps (the non-Bayesian ablation) keep {S, W, stamp}: a pair
+// adds (d, 1) to (S, W) and raises the 64-bit stamp scan << 40 | point << 8
+// | label with atomicMax, so the label of the last observation in scan, then
+// point order survives whatever order the reductions run in.
 #include "closed_common.cuh"
 #include "geometry.cuh"
 #include "hash.cuh"
@@ -81,16 +86,21 @@ __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_con
   const int64_t j = (int64_t)(t - J.tile_begin) * kDirectThreads + threadIdx.x;
   if (j >= J.n) return;
   Ray ry;
-  if (!ray_setup(J.g, __ldg(J.pts + 3 * j), __ldg(J.pts + 3 * j + 1), __ldg(J.pts + 3 * j + 2),
-                 ry))
-    return;
+  if (!ray_setup_at(J.g, J.pts, j, ry)) return;
   const uint32_t cls = argmax_row(J.sem + (size_t)j * J.K, J.K);
   uint32_t slot = kFailSlot;
+  const unsigned long long stamp = ((unsigned long long)J.g.scan_no << 40) |
+                                   ((unsigned long long)(uint32_t)j << 8) | cls;
   ray_for_each_blk(J.g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d, bool new_block) {
     if (new_block) slot = map_block_slot(mv, pack_block(i0 >> 3, i1 >> 3, i2 >> 3));
     if (slot >= mv.block_cap) return;
     float* r = mv.rec + ((size_t)slot * kBlockVoxels + local_index(i0, i1, i2)) * mv.rs;
-    red_add_v2(r + 2 * cls, d, 1.f);
+    if (J.latest) {
+      red_add_v2(r, d, 1.f);
+      atomicMax(reinterpret_cast<unsigned long long*>(r + 2), stamp);
+    } else {
+      red_add_v2(r + 2 * cls, d, 1.f);
+    }
   });
 }
 
@@ -108,7 +118,7 @@ cudaError_t launch_direct_batch(HashBatch& b, cudaStream_t st) {
 }
 
 cudaError_t launch_fuse_direct(const MapView& mv, const ScanGeom& g, const float* pts,
-                               const float* sem, int64_t n, int K, cudaStream_t st) {
+                               const float* sem, int64_t n, int K, int latest, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   HashBatch b;
   b.n_jobs = 1;
@@ -119,6 +129,7 @@ cudaError_t launch_fuse_direct(const MapView& mv, const ScanGeom& g, const float
   b.job[0].n = n;
   b.job[0].K = K;
   b.job[0].band_blocks = 0;
+  b.job[0].latest = latest;
   b.work = mv.ctr + kCtrWork;
   return launch_direct_batch(b, st);
 }

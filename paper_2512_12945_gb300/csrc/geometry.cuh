@@ -81,6 +81,30 @@ __device__ __forceinline__ bool ray_setup(const ScanGeom& g, float p0, float p1,
   return true;
 }
 
+// ray_setup for point j of a scan: read from the AoS array pts, or (depth
+// front end) back-projected from pixel (u, v) = (j mod dw, j div dw) of the
+// z-depth image as (((u + 0.5) - cx) / fx * z, ((v + 0.5) - cy) / fy * z, z)
+// in this FP32 op order; a non-finite or non-positive depth is invalid.
+__device__ __forceinline__ bool ray_setup_at(const ScanGeom& g, const float* __restrict__ pts,
+                                             int64_t j, Ray& ry) {
+  float p0, p1, p2;
+  if (g.depth) {
+    const float z = __ldg(g.depth + j);
+    if (!(z > 0.0f) || !isfinite(z)) return false;
+    const int32_t u = (int32_t)(j % g.dw), v = (int32_t)(j / g.dw);
+    const float xu = __fdiv_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), g.cx), g.fx);
+    const float yv = __fdiv_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), g.cy), g.fy);
+    p0 = __fmul_rn(xu, z);
+    p1 = __fmul_rn(yv, z);
+    p2 = z;
+  } else {
+    p0 = __ldg(pts + 3 * j);
+    p1 = __ldg(pts + 3 * j + 1);
+    p2 = __ldg(pts + 3 * j + 2);
+  }
+  return ray_setup(g, p0, p1, p2, ry);
+}
+
 // Along-ray SDF of the current voxel's centre: d = (x - c) . u.
 __device__ __forceinline__ float ray_sdf(const Ray& ry, float v) {
   float c0 = __fmul_rn(__fadd_rn((float)ry.i0, 0.5f), v);

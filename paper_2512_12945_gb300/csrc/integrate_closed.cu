@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_traverse_alloc(MapView mv, ScanGeom g,
   int cnt = 0;
   if (j < n) {
     Ray ry;
-    if (ray_setup(g, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], ry)) {
+    if (ray_setup_at(g, pts, j, ry)) {
       uint64_t last = kEmptyKey;
       ray_for_each(g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float) {
         const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256, 2)
   uint8_t mycls = 0;
   if (tid < tile_points && j < n) {
     Ray ry;
-    if (ray_setup(g, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], ry)) {
+    if (ray_setup_at(g, pts, j, ry)) {
       const float* srow = sem + (size_t)j * K;
       if (MODE == 0) {
         int best = 0;

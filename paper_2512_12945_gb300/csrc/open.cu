@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) k_open_pairs(MapView mv, ScanGeom g,
   const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
   int cnt = 0, np = 0;
   Ray ry;
-  const bool valid = j < n && ray_setup(g, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], ry);
+  const bool valid = j < n && ray_setup_at(g, pts, j, ry);
   if (valid) {
     Ray r2 = ry;
     uint64_t last = kEmptyKey;

@@ -28,7 +28,7 @@ struct RenderArgs {
   int32_t width, height;
   float t0, t1, v;
   int32_t cap;  // 3 ceil((far - near) / v) + 3
-  int32_t open, K, L, bf16;
+  int32_t open, latest, K, L, bf16;
   const float* q;  // open set: l-vector or null
   float* depth;
   int32_t* ijk;
@@ -144,7 +144,11 @@ __global__ void __launch_bounds__(256) k_render(const __grid_constant__ RenderAr
           a.ijk[3 * pix + 2] = ry.i2;
         }
         int32_t lab = -1;
-        if (!a.open) {
+        if (a.latest) {
+          const size_t vox = (size_t)slot * kBlockVoxels + local_index(ry.i0, ry.i1, ry.i2);
+          const float* r = mv.rec + vox * mv.rs;
+          lab = (int32_t)(*reinterpret_cast<const unsigned long long*>(r + 2) & 0xFF);
+        } else if (!a.open) {
           const size_t vox = (size_t)slot * kBlockVoxels + local_index(ry.i0, ry.i1, ry.i2);
           const float* r = mv.rec + vox * mv.rs;
           const float* cnt = mv.split ? r + 1 : r + 2;
@@ -208,6 +212,7 @@ slim_status run_render(slim_map* m, const double world_from_camera[16], float fx
   a.v = m->p.voxel_size;
   a.cap = 3 * (int32_t)std::ceil(((double)far_t - (double)near_t) / (double)a.v) + 3;
   a.open = m->mode == SLIM_OPEN ? 1 : 0;
+  a.latest = m->mode == SLIM_CLOSED_LATEST ? 1 : 0;
   a.K = m->K;
   a.L = m->L;
   a.bf16 = m->bf16 ? 1 : 0;

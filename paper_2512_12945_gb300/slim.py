@@ -18,11 +18,12 @@ import torch
 
 from . import build as _build
 
-SLIM_CLOSED_ONEHOT, SLIM_CLOSED_SOFT, SLIM_OPEN = 0, 1, 2
+SLIM_CLOSED_ONEHOT, SLIM_CLOSED_SOFT, SLIM_OPEN, SLIM_CLOSED_LATEST = 0, 1, 2, 3
 SLIM_STORE_F32, SLIM_STORE_BF16 = 0, 1
 SLIM_EXTRACT_POSTERIOR = 1
 AGGREGATION = {"auto": 0, "sort": 1, "hash": 2, "direct": 3}
-MODES = {"onehot": SLIM_CLOSED_ONEHOT, "soft": SLIM_CLOSED_SOFT, "open": SLIM_OPEN}
+MODES = {"onehot": SLIM_CLOSED_ONEHOT, "soft": SLIM_CLOSED_SOFT, "open": SLIM_OPEN,
+         "latest": SLIM_CLOSED_LATEST}
 STATUS = {0: "SLIM_OK", 1: "SLIM_ERR_ARG", 2: "SLIM_ERR_CUDA", 3: "SLIM_ERR_CAPACITY",
           4: "SLIM_ERR_TIMEOUT", 5: "SLIM_ERR_NOMEM", 6: "SLIM_ERR_UNSUPPORTED",
           7: "SLIM_ERR_INTERNAL"}
@@ -60,7 +61,7 @@ EXPORTS = ["slim_map_params_default", "slim_map_create", "slim_map_destroy", "sl
            "slim_integrate", "slim_integrate_host", "slim_map_sync", "slim_map_stats",
            "slim_extract_tsdf", "slim_query", "slim_backward", "slim_integrate_batch",
            "slim_profile_enable", "slim_profile_read", "slim_autotune", "slim_query_rows_static",
-           "slim_extract_uncertainty", "slim_render", "slim_last_error"]
+           "slim_extract_uncertainty", "slim_render", "slim_integrate_depth", "slim_last_error"]
 KERNELS = ["traverse", "fuse_closed", "open_pairs", "open_apply", "query", "backward", "batch",
            "reset", "render"]
 N_KINDS = 16
@@ -104,6 +105,7 @@ def lib():
             "slim_query_rows_static": [P, I64, I32, P, I32, F, F, P, P, P],
             "slim_extract_uncertainty": [P, P, I64, ctypes.POINTER(I64), P],
             "slim_render": [P, P, F, F, F, F, I32, I32, F, F, P, P, P, P, P, P],
+            "slim_integrate_depth": [P, P, I32, I32, F, F, F, F, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -171,6 +173,16 @@ def slim_integrate(h, pts, pose, sem, width, stream=None):
     p_sem = _dev_ptr(sem, torch.float32, "sem", (n, width))
     keep, p_pose = _pose_arr(pose)
     _check(lib().slim_integrate(h, p_pts, n, p_pose, p_sem, _stream(stream)), "slim_integrate")
+
+
+def slim_integrate_depth(h, depth, fx, fy, cx, cy, pose, sem, width, stream=None):
+    """depth: (H, W) float32 z-depth on the device; sem: (H*W, width)."""
+    H, W = depth.shape
+    keep, p_pose = _pose_arr(pose)
+    _check(lib().slim_integrate_depth(h, _dev_ptr(depth, torch.float32, "depth", (H, W)), W, H,
+                                      float(fx), float(fy), float(cx), float(cy), p_pose,
+                                      _dev_ptr(sem, torch.float32, "sem", (H * W, width)),
+                                      _stream(stream)), "slim_integrate_depth")
 
 
 def slim_integrate_host(h, pts, pose, sem, width, stream=None):
@@ -401,6 +413,9 @@ class Map:
 
     def integrate(self, pts, pose, sem, stream=None):
         slim_integrate(self.handle, pts, pose, sem, self.width, stream)
+
+    def integrate_depth(self, depth, fx, fy, cx, cy, pose, sem, stream=None):
+        slim_integrate_depth(self.handle, depth, fx, fy, cx, cy, pose, sem, self.width, stream)
 
     def integrate_host(self, pts, pose, sem, stream=None):
         slim_integrate_host(self.handle, pts, pose, sem, self.width, stream)

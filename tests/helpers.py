@@ -10,7 +10,8 @@ RTOL, ATOL = 1e-5, 1e-6
 
 def oracle_map(w, mode=None, fp64=False, **kw):
     mode = w.mode if mode is None else mode
-    mcode = {"onehot": oracle.CLOSED_ONEHOT, "soft": oracle.CLOSED_SOFT, "open": oracle.OPEN}[mode]
+    mcode = {"onehot": oracle.CLOSED_ONEHOT, "soft": oracle.CLOSED_SOFT, "open": oracle.OPEN,
+             "latest": oracle.CLOSED_LATEST}[mode]
     m = oracle.OracleMap(voxel_size=w.voxel_size, trunc=w.trunc, mode=mcode,
                          num_classes=w.num_classes, embed_dim=w.embed_dim,
                          min_range=w.min_range, max_range=w.max_range,

@@ -186,3 +186,29 @@ def test_direct_batch_matches_oracle():
     for m, wk in zip(maps, (w, r)):
         m.sync()
         compare_closed(to_np(m.extract()), oracle_map(wk).extract(), "onehot")
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_latest_label_mode_matches_oracle(batched):
+    """The non-Bayesian ablation (latest measurement wins): the label each
+    voxel keeps is the oracle's last writer, bit for bit, whatever order the
+    reductions run in; scans of one map in one batched launch keep their
+    order through the scan stamp."""
+    from paper_2512_12945_gb300 import slim
+    w = synth.street_lidar(n_scans=4, n_az=512)
+    if batched:
+        m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, mode="latest",
+                     num_classes=w.num_classes, min_range=w.min_range, max_range=w.max_range,
+                     body_from_sensor=w.body_from_sensor,
+                     max_points=max(s["pts"].shape[0] for s in w.scans))
+        slim.slim_integrate_batch([(m, torch.from_numpy(s["pts"]).cuda(), s["pose"],
+                                    torch.from_numpy(s["sem"]).cuda()) for s in w.scans])
+        m.sync()
+    else:
+        m = gpu_map(w, mode="latest")
+    g = to_np(m.extract())
+    o = oracle_map(w, mode="latest").extract()
+    compare_closed(g, o, "onehot")
+    with pytest.raises(slim.SlimError) as e:
+        m.uncertainty()
+    assert e.value.status == 6

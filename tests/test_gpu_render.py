@@ -91,3 +91,11 @@ def test_render_empty_map_and_bad_args():
         with pytest.raises(slim.SlimError) as e:
             m.render(**kw)
         assert e.value.status == 1
+
+
+def test_render_latest_label_map():
+    w = synth.street_lidar(n_scans=3, n_az=1024)
+    m = gpu_map(w, mode="latest")
+    om = oracle_map(w, mode="latest")
+    args = (_cam([3.0, 0.0, 1.6]), 100.0, 100.0, 80.0, 60.0, 160, 120, 0.5, 60.0)
+    _compare(m.render(*args), om.render(*args))
