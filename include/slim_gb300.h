@@ -270,10 +270,11 @@ slim_status slim_query(slim_map* m, const uint16_t* q_dev, int32_t q, float temp
  *             aligned); q_dev q x l bf16 queries (16-byte aligned);
  *   label_dev, prob_dev  n_rows outputs as in slim_query.
  * It calls no cudaMalloc / cudaFree and no allocating library routine: its
- * working memory (query and row norms, a status word) is one static array
- * in device memory, present on every GPU that loads the library until the
- * process exits, sized for at most 2^20 rows and 256 queries per call;
- * larger requests return SLIM_ERR_ARG. The first call on a device looks up
+ * working memory (query norms, a status word) is one static array in device
+ * memory, present on every GPU that loads the library until the process
+ * exits; the row norms are computed inside the query kernel from the tiles
+ * it already loads. At most 2^20 rows and 256 queries per call; larger
+ * requests return SLIM_ERR_ARG. The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress, with the device
  * current) and opts the query kernel into its shared memory; make that first
  * call before any stream capture. Every call shares the array and leaves its

@@ -17,6 +17,9 @@
 //               trees, argmax; the odd-chunk warp hands its (max, sum,
 //               argmax) to the even-chunk warp through shared memory, which
 //               combines them, applies the threshold and writes the row.
+//   warps 10-11 (caller-held rows) row norms |m|^2 from the A stages in
+//               shared memory, 64 rows each, handed to the epilogue per
+//               accumulator.
 //
 // The grid is persistent (one CTA per SM, tiles strided over CTAs). Every
 // mbarrier wait is bounded: running out raises the map status, the CTA stops
@@ -34,7 +37,7 @@ namespace slim {
 constexpr int kQM = 128;        // voxel rows per tile
 constexpr int kQK = 64;         // K elements per stage (128-byte rows)
 constexpr int kQStages = 4;
-constexpr int kQThreads = 320;  // 10 warps: TMA, MMA, 8 epilogue
+constexpr int kQThreads = 384;  // 12 warps: TMA, MMA, 8 epilogue, 2 row norms
 constexpr uint64_t kWaitNs = 500ull * 1000 * 1000;  // a wait gives up after 0.5 s
 
 struct QueryArgs {
@@ -47,7 +50,8 @@ struct QueryArgs {
   float temp_log2e;     // T / log2(e): turns a base-2 logit back into a cosine
   float tp;
   const float* qinv;    // [Q] 1 / |q|
-  const float* rnorm2;  // [n_rows] |m|^2
+  const float* rnorm2;  // [n_rows] |m|^2, or null when fuse_norms
+  int32_t fuse_norms;   // compute |m|^2 from the A tiles in shared memory
   int32_t* label;
   float* prob;
   float* scores;        // [n_rows x Q] cosines or null
@@ -240,12 +244,14 @@ __global__ void __launch_bounds__(kQThreads, 1)
   uint64_t* tfull = bars + 2 * kQStages;
   uint64_t* tempty = bars + 2 * kQStages + 2;
   uint64_t* hdone = bars + 2 * kQStages + 4;  // [quarter][accumulator]: odd half handed over
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kQStages + 12);
+  uint64_t* nready = bars + 2 * kQStages + 12;  // [accumulator]: the tile's row norms written
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kQStages + 14);
   volatile uint32_t* abort_flag = tmem_slot + 1;
   float* s_qinv = reinterpret_cast<float*>(tmem_slot + 4);
   float* part_m = s_qinv + 256;  // [accumulator][128 rows]: odd half's running max
   float* part_s = part_m + 256;  //                          running sum
   int* part_b = reinterpret_cast<int*>(part_s + 256);  //   argmax
+  float* rn = reinterpret_cast<float*>(part_b + 256);   // [accumulator][128 rows] |m|^2
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t num_tiles = (a.n_rows + kQM - 1) / kQM;
@@ -258,13 +264,14 @@ __global__ void __launch_bounds__(kQThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kQStages; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&empty[s]), a.fuse_norms ? 3 : 1);  // MMA commit (+ 2 norm warps)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(smem_u32(&tfull[s]), 1);
       mbar_init(smem_u32(&tempty[s]), 8);
     }
     for (int s = 0; s < 8; ++s) mbar_init(smem_u32(&hdone[s]), 1);
+    for (int s = 0; s < 2; ++s) mbar_init(smem_u32(&nready[s]), 2);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
@@ -366,6 +373,75 @@ __global__ void __launch_bounds__(kQThreads, 1)
     }
     // the MMAs must be complete before TMEM is freed
     if (committed_any) mbar_wait(last_commit_bar, last_commit_phase);
+  } else if (warp >= 10) {
+    // ---------------------------------------------------------- row norms
+    // |m|^2 of each row from the A stages the MMA consumes: a 128-byte
+    // swizzled row keeps its 16-byte chunks within the row, so a row's sum
+    // of squares is the sum over its 128 bytes. Warp 10 + h takes rows
+    // [64 h, 64 h + 64); lane l reads chunk l % 8 of rows 64 h + 4 i + l / 8
+    // (one warp load covers 4 whole rows: no bank conflicts); the stage is
+    // released after the read (the empty barrier counts both norm warps and
+    // the MMA commit).
+    const int rbase = (warp - 10) * 64;
+    if (a.fuse_norms) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+        float part[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) part[i] = 0.f;
+        bool ok = true;
+        for (int kc = 0; kc < kchunks; ++kc) {
+          ok = mbar_wait(smem_u32(&full[stage]), phase);
+          ok = __all_sync(0xFFFFFFFFu, ok);
+          if (!ok) break;
+          const unsigned char* sa =
+              sA + stage * bytesA + (rbase + (lane >> 3)) * 128 + (lane & 7) * 16;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const uint4 v = *reinterpret_cast<const uint4*>(sa + i * 4 * 128);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[h]));
+              part[i] += f.x * f.x + f.y * f.y;
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&empty[stage]));
+          if (++stage == kQStages) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        // the epilogue has read the norms of tile - 2 before releasing acc
+        if (ok) ok = __all_sync(0xFFFFFFFFu, mbar_wait(smem_u32(&tempty[acc]), acc_phase ^ 1));
+        if (!ok) {
+          if (lane == 0) {
+            *abort_flag = 1;
+            raise_status(a.status, kDevTimeout, 25);
+          }
+          break;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          part[i] += __shfl_xor_sync(0xFFFFFFFFu, part[i], 1);
+          part[i] += __shfl_xor_sync(0xFFFFFFFFu, part[i], 2);
+          part[i] += __shfl_xor_sync(0xFFFFFFFFu, part[i], 4);
+        }
+        if ((lane & 7) == 0)
+#pragma unroll
+          for (int i = 0; i < 16; ++i) rn[acc * kQM + rbase + 4 * i + (lane >> 3)] = part[i];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&nready[acc]));
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
+      }
+    }
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue
     const int quarter = warp & 3;      // the TMEM lane quarter this warp may read
@@ -375,6 +451,7 @@ __global__ void __launch_bounds__(kQThreads, 1)
     uint32_t acc_phase = 0;
     for (uint32_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
       bool ok = mbar_wait(smem_u32(&tfull[acc]), acc_phase);
+      if (ok && a.fuse_norms) ok = mbar_wait(smem_u32(&nready[acc]), acc_phase);
       ok = __all_sync(0xFFFFFFFFu, ok);
       if (!ok) {
         if (lane == 0) {
@@ -386,7 +463,7 @@ __global__ void __launch_bounds__(kQThreads, 1)
       tc_fence_after();
       const uint32_t row = tile * kQM + rl;
       const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * a.N);
-      const float n2 = row < a.n_rows ? a.rnorm2[row] : 0.f;
+      const float n2 = a.fuse_norms ? rn[acc * kQM + rl] : (row < a.n_rows ? a.rnorm2[row] : 0.f);
       const float rinv = n2 > 0.f ? rsqrtf(n2) : 0.f;
       float* srow = (a.scores && row < a.n_rows) ? a.scores + (size_t)row * a.Q : nullptr;
       // base-2 logits: colscale = |q|^-1 log2(e) / T, rowscale = |m|^-1
@@ -563,8 +640,8 @@ static bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t
 }
 
 size_t query_smem_bytes(int N) {
-  return 1024 + (size_t)kQStages * (kQM * 128 + (size_t)N * 128) + (2 * kQStages + 12) * 8 + 16 +
-         256 * 4 + 3 * 256 * 4;
+  return 1024 + (size_t)kQStages * (kQM * 128 + (size_t)N * 128) + (2 * kQStages + 14) * 8 + 16 +
+         256 * 4 + 3 * 256 * 4 + 256 * 4;
 }
 
 cudaError_t query_setup_attributes() {
@@ -607,6 +684,7 @@ slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float tempe
   a.tp = tp;
   a.qinv = m->qscratch.qinv;
   a.rnorm2 = rn2;
+  a.fuse_norms = 0;
   a.label = label;
   a.prob = prob;
   a.scores = scores;
@@ -630,8 +708,10 @@ slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float tempe
 // budget is fixed up front, or host programs that only hand in buffers they
 // already own. slim_query_rows_static serves them: its working memory is the
 // file-scope array below, which exists on every GPU that loads this library
-// for as long as the process lives. It holds the inverse query norms, the
-// row norms of at most kStaticQueryRows rows, and a status word.
+// for as long as the process lives. It holds the inverse query norms and a
+// status word (the row norms are computed inside k_query from the A tiles);
+// the region sized for the norms of kStaticQueryRows rows is kept as the
+// per-call row limit.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kStaticQueryRows = 1u << 20;  // rows per call (4 MiB of row norms)
 constexpr uint32_t kStaticQueries = 256;
@@ -697,8 +777,6 @@ extern "C" slim_status slim_query_rows_static(const uint16_t* rows_dev, int64_t 
   e = cudaMemsetAsync(status, 0, kNumCounters * sizeof(uint32_t), st);
   if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
   const uint32_t rows = (uint32_t)n_rows;
-  k_row_norms_bf16<<<(unsigned)(((uint64_t)rows * 32 + 255) / 256), 256, 0, st>>>(
-      reinterpret_cast<const __nv_bfloat16*>(rows_dev), rnorm2, rows, l);
   k_query_norms<<<(q * 32 + 255) / 256, 256, 0, st>>>(
       reinterpret_cast<const __nv_bfloat16*>(q_dev), q, l, qinv);
   const int N = (q + 15) / 16 * 16;
@@ -718,7 +796,8 @@ extern "C" slim_status slim_query_rows_static(const uint16_t* rows_dev, int64_t 
   a.temp_log2e = temperature / 1.4426950408889634f;
   a.tp = tp;
   a.qinv = qinv;
-  a.rnorm2 = rnorm2;
+  a.rnorm2 = nullptr;  // the row norms are computed inside the kernel
+  a.fuse_norms = 1;
   a.label = label_dev;
   a.prob = prob_dev;
   a.scores = nullptr;
