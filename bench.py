@@ -79,6 +79,21 @@ def dist_env():
 
 
 # ----------------------------------------------------------------- helpers
+def max_over_ranks(ms, dist, device="cuda"):
+    """The slowest rank's time (replicas: the job ends with its last rank)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(ws, units_per_rank, ms_max):
+    """Whole-job throughput of ws independent replicas: all units processed
+    over the slowest rank's time."""
+    return ws * units_per_rank / (ms_max / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 50 ms."""
 
@@ -348,10 +363,7 @@ def run_ours(args):
     clocks.stop()
     stats = m.stats()
 
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, dist)
 
     counts = None
     try:
@@ -364,7 +376,7 @@ def run_ours(args):
     else:
         valid_per_step = int(sum(int((np.linalg.norm(s["pts"], axis=1) >= w.min_range).sum())
                                  for s in w.scans))
-    value = ws * valid_per_step * args.steps / (ms_max / 1e3)
+    value = replica_rate(ws, valid_per_step * args.steps, ms_max)
 
     # roofline of the dominant kernel (the batched integration kernel of the
     # autotuned strategy): algorithmic bytes of the scans one launch
@@ -458,11 +470,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     e_ms = max(e0.elapsed_time(e1), wall * 1e3)
-    et = torch.tensor([e_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e_ms = float(et.item())
-    e2e = {"value": ws * valid_per_step * n_e2e / (e_ms / 1e3), "unit": UNIT,
+    e_ms = max_over_ranks(e_ms, dist)
+    e2e = {"value": replica_rate(ws, valid_per_step * n_e2e, e_ms), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * 4, "steps": n_e2e,
            "call": "pinned host -> device copies of 16-scan chunks on a copy stream, "
                    "overlapped with slim_integrate_batch of the previous chunk, + slim_map_stats"}

@@ -233,6 +233,7 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   if ((s = m->alloc(&mv.hvals, nh)) != SLIM_OK) return bail(s);
   if ((s = m->alloc(&mv.blk_key, bc)) != SLIM_OK) return bail(s);
   if ((s = m->alloc(&mv.ctr, (size_t)kNumCounters)) != SLIM_OK) return bail(s);
+  if ((s = m->alloc(&m->render_bounds, (size_t)6)) != SLIM_OK) return bail(s);
   mv.entry_mask = (uint32_t)(m->n_entries - 1);
   mv.max_probe = (int32_t)std::min<uint64_t>(m->n_entries, 512);
   mv.block_cap = (uint32_t)bc;

@@ -22,6 +22,7 @@ namespace slim {
 
 struct RenderArgs {
   MapView mv;
+  const int32_t* bounds;  // min bx, by, bz, max bx, by, bz of the allocated blocks
   float R[9];  // world_from_camera rotation (FP32)
   float o[3];  // camera centre
   float fx, fy, cx, cy;
@@ -95,12 +96,20 @@ __global__ void __launch_bounds__(256) k_render(const __grid_constant__ RenderAr
     ry.m0 = tm[0]; ry.m1 = tm[1]; ry.m2 = tm[2];
     ry.e0 = td[0]; ry.e1 = td[1]; ry.e2 = td[2];
   }
+  // the allocated blocks' bounding box: once the ray is beyond it on an
+  // axis it does not travel back along, no later voxel can be observed
+  const int32_t lo0 = a.bounds[0], lo1 = a.bounds[1], lo2 = a.bounds[2];
+  const int32_t hi0 = a.bounds[3], hi1 = a.bounds[4], hi2 = a.bounds[5];
   bool fresh = true, have_prev = false;
   uint32_t slot = kNoSlot;
   float Dp = 0.f, tp = 0.f;
   for (int k = 0; k < a.cap; ++k) {
     if (fresh) {
-      slot = hash_find(mv, pack_block(ry.i0 >> 3, ry.i1 >> 3, ry.i2 >> 3));
+      const int32_t b0 = ry.i0 >> 3, b1 = ry.i1 >> 3, b2 = ry.i2 >> 3;
+      if ((b0 > hi0 && ry.s0 >= 0) || (b0 < lo0 && ry.s0 <= 0) || (b1 > hi1 && ry.s1 >= 0) ||
+          (b1 < lo1 && ry.s1 <= 0) || (b2 > hi2 && ry.s2 >= 0) || (b2 < lo2 && ry.s2 <= 0))
+        break;
+      slot = hash_find(mv, pack_block(b0, b1, b2));
       fresh = false;
     }
     float W = 0.f, D = 0.f;
@@ -191,12 +200,50 @@ __global__ void __launch_bounds__(256) k_render(const __grid_constant__ RenderAr
   if (a.sim) a.sim[pix] = 0.f;
 }
 
+// Bounding box of the allocated blocks (slots below the allocation counter).
+__global__ void __launch_bounds__(256) k_block_bounds(const uint64_t* __restrict__ blk_key,
+                                                      const uint32_t* ctr, uint32_t block_cap,
+                                                      int32_t* bounds) {
+  const uint32_t nb = min(*(volatile const uint32_t*)&ctr[kCtrBlocks], block_cap);
+  int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < nb; s += gridDim.x * blockDim.x) {
+    int32_t b[3];
+    unpack_block(blk_key[s], b[0], b[1], b[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = min(lo[k], b[k]);
+      hi[k] = max(hi[k], b[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      lo[k] = min(lo[k], __shfl_xor_sync(0xFFFFFFFFu, lo[k], off));
+      hi[k] = max(hi[k], __shfl_xor_sync(0xFFFFFFFFu, hi[k], off));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&bounds[k], lo[k]);
+      atomicMax(&bounds[3 + k], hi[k]);
+    }
+  }
+}
+
+__global__ void k_bounds_init(int32_t* bounds) {
+  if (threadIdx.x < 3) bounds[threadIdx.x] = INT32_MAX;
+  else if (threadIdx.x < 6) bounds[threadIdx.x] = INT32_MIN;
+}
+
 slim_status run_render(slim_map* m, const double world_from_camera[16], float fx, float fy,
                        float cx, float cy, int32_t width, int32_t height, float near_t,
                        float far_t, const float* q, float* depth, int32_t* ijk, int32_t* label,
                        float* sim, cudaStream_t st) {
   RenderArgs a;
   a.mv = m->mv;
+  a.bounds = m->render_bounds;
   for (int r = 0; r < 3; ++r) {
     for (int c = 0; c < 3; ++c) a.R[r * 3 + c] = (float)world_from_camera[r * 4 + c];
     a.o[r] = (float)world_from_camera[r * 4 + 3];
@@ -223,6 +270,9 @@ slim_status run_render(slim_map* m, const double world_from_camera[16], float fx
   a.sim = sim;
   const int64_t n = (int64_t)width * height;
   const int tok = prof_begin(m, SLIM_KERNEL_RENDER, st);
+  k_bounds_init<<<1, 32, 0, st>>>(m->render_bounds);
+  k_block_bounds<<<152 * 2, 256, 0, st>>>(m->mv.blk_key, m->mv.ctr, m->mv.block_cap,
+                                         m->render_bounds);
   k_render<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
   prof_end(m, tok, st);
   const cudaError_t e = cudaGetLastError();
