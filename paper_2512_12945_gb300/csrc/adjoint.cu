@@ -10,9 +10,9 @@
 //   open: m_v = sum z / W_v, beta_v = 1/2 sum (z - m_v)^2
 //                               ->  dL/dz_j += dL/dm_v / W_v
 //                                              + dL/dbeta_v * (z_j - m_v)
-// One warp per point: every lane walks the same DDA, lanes split the class
-// or embedding dimension; the result is a gather (the adjoint of the
-// forward scatter), so no atomics are needed.
+// Open set: one warp per point, every lane walks the same DDA and lanes
+// split the embedding dimension; closed set: one thread per point. The
+// result is a gather (the adjoint of the forward scatter), so no atomics.
 #include <cuda_bf16.h>
 
 #include "geometry.cuh"
@@ -107,6 +107,52 @@ __global__ void __launch_bounds__(256) k_backward(MapView mv, ScanGeom g,
   }
 }
 
+// Closed set: one thread per point (the class gradient of a pair is a
+// K-vector, so a warp per point would repeat the DDA 32 times). The thread
+// owns its output row dL/dsem_j and accumulates into it in pair order.
+__global__ void __launch_bounds__(256) k_backward_closed(MapView mv, ScanGeom g,
+                                                         const float* __restrict__ pts, int64_t n,
+                                                         int K, const float* __restrict__ gD,
+                                                         const float* __restrict__ gS,
+                                                         float* gsem, float* gxyz, int sem_grad) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float* out = gsem + (size_t)j * K;
+  for (int k = 0; k < K; ++k) out[k] = 0.f;
+  float gx0 = 0.f, gx1 = 0.f, gx2 = 0.f;
+  Ray ry;
+  if (ray_setup(g, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], ry)) {
+    uint64_t last = kEmptyKey;
+    uint32_t slot = kNoSlot;
+    ray_for_each(g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d) {
+      const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
+      if (kb != last) {
+        last = kb;
+        slot = hash_find(mv, kb);
+      }
+      if (slot >= mv.block_cap) return;
+      const size_t vox = (size_t)slot * kBlockVoxels + local_index(i0, i1, i2);
+      const float Wv = rec_weight(mv.rec + vox * mv.rs, mv.K, mv.split);
+      const float invW = 1.0f / Wv;
+      if (sem_grad)
+        for (int k = 0; k < K; ++k) out[k] += gS[vox * (size_t)K + k];
+      if (!(d < g.tau)) return;  // clamped at tau: no dependence on x
+      const float gd = gD[vox] * invW;
+      const float c0 = ((float)i0 + 0.5f) * g.v, c1 = ((float)i1 + 0.5f) * g.v,
+                  c2 = ((float)i2 + 0.5f) * g.v;
+      const float e0 = ry.x0 - c0, e1 = ry.x1 - c1, e2 = ry.x2 - c2;
+      const float eu = e0 * ry.u0 + e1 * ry.u1 + e2 * ry.u2;
+      const float ir = 1.0f / ry.r;
+      gx0 += gd * (ry.u0 + (e0 - ry.u0 * eu) * ir);
+      gx1 += gd * (ry.u1 + (e1 - ry.u1 * eu) * ir);
+      gx2 += gd * (ry.u2 + (e2 - ry.u2 * eu) * ir);
+    });
+  }
+  gxyz[3 * j + 0] = g.R[0] * gx0 + g.R[3] * gx1 + g.R[6] * gx2;
+  gxyz[3 * j + 1] = g.R[1] * gx0 + g.R[4] * gx1 + g.R[7] * gx2;
+  gxyz[3 * j + 2] = g.R[2] * gx0 + g.R[5] * gx1 + g.R[8] * gx2;
+}
+
 slim_status run_backward(slim_map* m, const ScanGeom& g, const float* pts, const float* sem,
                          int64_t n, const float* gD, const float* gS, const float* gB,
                          float* gsem, float* gxyz, cudaStream_t st) {
@@ -123,8 +169,8 @@ slim_status run_backward(slim_map* m, const ScanGeom& g, const float* pts, const
       k_backward<1, 0><<<grid, 256, 0, st>>>(m->mv, g, pts, sem, n, width, gD, gS, gB, gsem, gxyz,
                                              sg);
   } else {
-    k_backward<0, 0><<<grid, 256, 0, st>>>(m->mv, g, pts, sem, n, width, gD, gS, gB, gsem, gxyz,
-                                           sg);
+    k_backward_closed<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->mv, g, pts, n, width, gD,
+                                                                   gS, gsem, gxyz, sg);
   }
   prof_end(m, tok, st);
   const cudaError_t e = cudaGetLastError();

@@ -240,3 +240,31 @@ def test_benchmark_configuration_full_parity(_street100_oracle, agg):
     g = to_np(m.extract())
     assert len(g["W"]) > 1_900_000
     compare_closed(g, o, "onehot")
+
+
+@pytest.mark.parametrize("mode,agg", [("onehot", "direct"), ("onehot", "hash"),
+                                      ("onehot", "sort"), ("latest", "auto")])
+def test_max_classes_64(mode, agg):
+    """K = 64 (the largest class count: the class index fills the 6 class
+    bits of a hash-tile key and lives in the latest-label stamp's byte)."""
+    w = synth.room_lidar(n_scans=3, K=64)
+    g = to_np(gpu_map(w, mode=mode, aggregation=agg).extract())
+    o = oracle_map(w, mode=mode).extract()
+    compare_closed(g, o, "onehot")
+
+
+def test_hash_table_full_is_a_capacity_fault():
+    """A hash table too small for the scan's blocks: the probe limit raises
+    SLIM_ERR_CAPACITY on the sticky status (nothing hangs), reset clears it."""
+    from paper_2512_12945_gb300 import slim
+    w = synth.street_lidar(n_scans=1, n_az=512)
+    s = w.scans[0]
+    m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=20, min_range=w.min_range,
+                 max_range=w.max_range, body_from_sensor=w.body_from_sensor,
+                 max_points=s["pts"].shape[0], hash_capacity=32)
+    m.integrate(torch.from_numpy(s["pts"]).cuda(), s["pose"], torch.from_numpy(s["sem"]).cuda())
+    with pytest.raises(slim.SlimError) as e:
+        m.sync()
+    assert e.value.status == 3
+    m.reset()
+    m.sync()

@@ -102,3 +102,21 @@ def test_open_long_runs_split_across_pieces():
     g = to_np(gpu_map(w, voxel_capacity=400000).extract())
     o = oracle_map(w).extract()
     _compare(g, o)
+
+
+def test_open_max_dim_1024_bf16():
+    """l = 1024 (the largest embedding: 8 element chunks per pass loop) with
+    BF16 storage, against the oracle. Each scan rounds m and beta to BF16
+    (half an ulp each, 2^-9 relative); the next scan's beta update uses the
+    rounded m, which moves beta by another rounding of the same order, so
+    beta is bounded by one ulp (2^-8) of its largest magnitude per scan and
+    m by half an ulp per scan."""
+    w = _work(frames=2, w=48, h=36, dim=1024)
+    g = to_np(gpu_map(w, embed_storage="bf16", voxel_capacity=100000).extract())
+    o = oracle_map(w).extract()
+    assert np.array_equal(g["ijk"], o["ijk"])
+    assert np.array_equal(g["W"].astype(np.float64), o["W"])
+    n = len(w.scans)
+    for k, ulp in (("sem", 2.0 ** -9), ("beta", 2.0 ** -8)):
+        err = np.abs(g[k] - o[k])
+        assert err.max() <= n * ulp * np.abs(o[k]).max() + 1e-6, k
