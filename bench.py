@@ -726,6 +726,22 @@ def run_adjoint(args):
             t.grad = None
         loss.backward()
 
+    # the forward alone with each soft-count strategy (sort tiles, direct
+    # vector reductions) on maps of their own
+    fwd_by = {}
+    for agg in ("sort", "direct"):
+        mv = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, mode="soft", num_classes=20,
+                      min_range=w.min_range, max_range=w.max_range, max_points=131072,
+                      block_capacity=100000, hash_capacity=1 << 20, aggregation=agg)
+        det = [(p.detach(), q.detach()) for p, q in zip(pts, sem)]
+
+        def integ():
+            mv.reset()
+            for (p, q), po in zip(det, poses):
+                mv.integrate(p, po, q)
+
+        fwd_by[agg] = _timed(integ, args.steps, args.warmup, stream)
+        mv.close()
     fms = _timed(fwd, args.steps, args.warmup, stream)
     torch.cuda.reset_peak_memory_stats()
     base = torch.cuda.memory_allocated()
@@ -738,6 +754,7 @@ def run_adjoint(args):
             "config": {"workload": "room 20 scans x 64x2048, 20 classes soft counts, loss = "
                                    "sum D^2 + CE on 10k sampled voxels"},
             "forward_ms": fms, "forward_backward_ms": tms, "backward_ms": tms - fms,
+            "integrate_ms_by_strategy": fwd_by,
             "memory": {"saved_for_backward": "inputs only; (voxel, point) pairs recomputed",
                        "torch_peak_bytes_above_inputs": int(peak)}}
     print(json.dumps(line), flush=True)

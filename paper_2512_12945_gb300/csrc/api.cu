@@ -151,9 +151,8 @@ slim_status check_params(const slim_map_params* p) {
     return fail(SLIM_ERR_ARG, "aggregation must be 0 (auto), 1 (sort), 2 (hash) or 3 (direct)");
   if (p->aggregation == SLIM_AGG_HASH && p->mode != SLIM_CLOSED_ONEHOT)
     return fail(SLIM_ERR_ARG, "hash aggregation serves the closed one-hot mode only");
-  if (p->aggregation == SLIM_AGG_DIRECT && p->mode != SLIM_CLOSED_ONEHOT &&
-      p->mode != SLIM_CLOSED_LATEST)
-    return fail(SLIM_ERR_ARG, "direct aggregation serves the one-hot and latest-label modes");
+  if (p->aggregation == SLIM_AGG_DIRECT && p->mode == SLIM_OPEN)
+    return fail(SLIM_ERR_ARG, "direct aggregation serves the closed-set modes");
   if (p->mode == SLIM_CLOSED_LATEST && p->aggregation != SLIM_AGG_AUTO &&
       p->aggregation != SLIM_AGG_DIRECT)
     return fail(SLIM_ERR_ARG, "the latest-label mode uses direct reductions only");
@@ -199,11 +198,11 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   m->L = p->mode == SLIM_OPEN ? p->embed_dim : 0;
   m->bf16 = (p->mode == SLIM_OPEN && p->embed_storage == SLIM_STORE_BF16) ? 1 : 0;
   // one-hot records keep (S_k, c_k) per class, soft records (S, W, c_k)
-  // record floats: one-hot {S_k, c_k} per class; soft {S, W, c_k}; latest
-  // {S, W, stamp (u64)}
+  // record floats: one-hot {S_k, c_k} per class; soft {S, W, pad, pad, c_k}
+  // (counts 16-byte aligned for vector reductions); latest {S, W, stamp}
   m->rs = p->mode == SLIM_CLOSED_ONEHOT  ? (2 * m->K + 3) / 4 * 4
           : p->mode == SLIM_CLOSED_LATEST ? 4
-                                          : ((2 + m->K) + 3) / 4 * 4;
+                                          : ((kSoftCnt + m->K) + 3) / 4 * 4;
   const double q = 2.0 * (double)p->trunc / (double)p->voxel_size;
   m->cap = 3 * (int)std::ceil(q) + 3;
   const int span = (int)std::ceil(q) + 2;
@@ -216,6 +215,8 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   m->tile_points = closed_tile_points(m->cap, m->band_blocks);
   m->hash_tile = p->tile_points > 0 ? p->tile_points : 256;
   m->direct = p->mode == SLIM_CLOSED_LATEST ||
+              (p->mode == SLIM_CLOSED_SOFT &&
+               (p->aggregation == SLIM_AGG_DIRECT || p->aggregation == SLIM_AGG_AUTO)) ||
               (p->mode == SLIM_CLOSED_ONEHOT &&
                (p->aggregation == SLIM_AGG_DIRECT ||
                 (p->aggregation == SLIM_AGG_AUTO && p->tile_points == 0)));
@@ -311,7 +312,7 @@ slim_status slim_map_destroy(slim_map* m) {
 
 // Closed one-hot map integrated by direct per-pair reductions.
 static bool uses_direct(const slim_map* m) {
-  return (m->mode == SLIM_CLOSED_ONEHOT || m->mode == SLIM_CLOSED_LATEST) && m->direct;
+  return m->mode != SLIM_OPEN && m->direct;
 }
 
 // Closed one-hot map integrated by the shared-memory hash tiles.
@@ -357,7 +358,8 @@ slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
     const int tok = prof_begin(m, SLIM_KERNEL_FUSE_CLOSED, st);
     if (uses_direct(m))
       SLIM_CUDA(launch_fuse_direct(m->mv, g, pts_dev, sem, n, m->K,
-                                   m->mode == SLIM_CLOSED_LATEST ? 1 : 0, st));
+                                   m->mode == SLIM_CLOSED_LATEST ? 1 : 0,
+                                   m->mode == SLIM_CLOSED_SOFT ? 1 : 0, st));
     else if (uses_hash(m))
       SLIM_CUDA(launch_fuse_hash(m->mv, g, pts_dev, sem, n, m->K, m->hash_tile, m->band_blocks,
                                  st));
@@ -405,11 +407,12 @@ slim_status slim_integrate_depth(slim_map* m, const float* depth_dev, int32_t wi
     // one-hot and latest maps take the direct kernel (the hash tiles read
     // point arrays); soft counts the sort tiles
     const int tok = prof_begin(m, SLIM_KERNEL_FUSE_CLOSED, st);
-    if (m->mode == SLIM_CLOSED_SOFT)
+    if (m->mode == SLIM_CLOSED_SOFT && !m->direct)
       SLIM_CUDA(launch_fuse_closed(m->mv, g, nullptr, sem, n, m->mode, m->K, m->tile_points, st));
     else
       SLIM_CUDA(launch_fuse_direct(m->mv, g, nullptr, sem, n, m->K,
-                                   m->mode == SLIM_CLOSED_LATEST ? 1 : 0, st));
+                                   m->mode == SLIM_CLOSED_LATEST ? 1 : 0,
+                                   m->mode == SLIM_CLOSED_SOFT ? 1 : 0, st));
     prof_end(m, tok, st);
     return SLIM_OK;
   }
@@ -471,6 +474,7 @@ slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
     b.job[k].K = m->K;
     b.job[k].band_blocks = m->band_blocks;
     b.job[k].latest = 0;
+    b.job[k].soft = 0;
     b.job[k].g.scan_no = 1;
   }
   const bool prof = m->prof_on;
@@ -763,6 +767,7 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
       J.K = m->K;
       J.band_blocks = m->band_blocks;
       J.latest = m->mode == SLIM_CLOSED_LATEST ? 1 : 0;
+      J.soft = m->mode == SLIM_CLOSED_SOFT ? 1 : 0;
       if (nb.n_jobs == kMaxHashJobs) {
         slim_status s = flush_direct();
         if (s != SLIM_OK) return s;
@@ -777,6 +782,7 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
                    m->p.min_range, m->p.max_range, m->cap);
       J.g.scan_no = (uint32_t)m->scans;
       J.latest = 0;
+      J.soft = 0;
       J.mv = m->mv;
       J.pts = it.pts_dev;
       J.sem = static_cast<const float*>(it.sem_dev);

@@ -9,6 +9,7 @@ constexpr uint64_t kEmptyKey = ~0ull;     // empty hash entry
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu; // hash entry without a block slot (yet)
 constexpr uint32_t kFailSlot = 0xFFFFFFFEu; // block could not get a slot (capacity)
 constexpr int kBlockVoxels = 512;         // 8^3 voxels per block
+constexpr int kSoftCnt = 4;  // soft-count records {S, W, pad, pad, c_0..}: counts 16-byte aligned
 
 // Device counters held by each map.
 enum Counter : int {
@@ -113,6 +114,13 @@ __device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
 }
 
 // Weight W of a closed-set voxel record.
+// r[0..3] += (a, b, c, d) without a return value (16-byte aligned).
+__device__ __forceinline__ void red_add_v4(float* r, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(r), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+
 __device__ __forceinline__ float rec_weight(const float* r, int K, int split) {
   if (!split) return r[1];
   float w = 0.f;

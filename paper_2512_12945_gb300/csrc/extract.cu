@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_extract_write(MapView mv, const uint32_
     } else if (!open) {
       const float* r = mv.rec + ((size_t)slot * kBlockVoxels + l) * mv.rs;
       // one-hot records hold (S_k, c_k) pairs, soft records (S, W, c_k)
-      const float* cnt = mv.split ? r + 1 : r + 2;
+      const float* cnt = mv.split ? r + 1 : r + kSoftCnt;
       const int cs = mv.split ? 2 : 1;
       float S = 0.f, W = 0.f;
       if (mv.split) {

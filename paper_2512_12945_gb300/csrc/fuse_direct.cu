@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_con
   if (j >= J.n) return;
   Ray ry;
   if (!ray_setup_at(J.g, J.pts, j, ry)) return;
-  const uint32_t cls = argmax_row(J.sem + (size_t)j * J.K, J.K);
+  const uint32_t cls = J.soft ? 0u : argmax_row(J.sem + (size_t)j * J.K, J.K);
   uint32_t slot = kFailSlot;
   const unsigned long long stamp = ((unsigned long long)J.g.scan_no << 40) |
                                    ((unsigned long long)(uint32_t)j << 8) | cls;
@@ -98,6 +98,17 @@ __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_con
     if (J.latest) {
       red_add_v2(r, d, 1.f);
       atomicMax(reinterpret_cast<unsigned long long*>(r + 2), stamp);
+    } else if (J.soft) {
+      // soft counts: (S, W) += (d, 1) and c += p, four classes per reduction
+      red_add_v2(r, d, 1.f);
+      const float* p = J.sem + (size_t)j * J.K;
+      for (int k = 0; k < J.K; k += 4) {
+        const float a0 = __ldg(p + k);
+        const float a1 = k + 1 < J.K ? __ldg(p + k + 1) : 0.f;
+        const float a2 = k + 2 < J.K ? __ldg(p + k + 2) : 0.f;
+        const float a3 = k + 3 < J.K ? __ldg(p + k + 3) : 0.f;
+        red_add_v4(r + kSoftCnt + k, a0, a1, a2, a3);
+      }
     } else {
       red_add_v2(r + 2 * cls, d, 1.f);
     }
@@ -118,7 +129,8 @@ cudaError_t launch_direct_batch(HashBatch& b, cudaStream_t st) {
 }
 
 cudaError_t launch_fuse_direct(const MapView& mv, const ScanGeom& g, const float* pts,
-                               const float* sem, int64_t n, int K, int latest, cudaStream_t st) {
+                               const float* sem, int64_t n, int K, int latest, int soft,
+                               cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   HashBatch b;
   b.n_jobs = 1;
@@ -130,6 +142,7 @@ cudaError_t launch_fuse_direct(const MapView& mv, const ScanGeom& g, const float
   b.job[0].K = K;
   b.job[0].band_blocks = 0;
   b.job[0].latest = latest;
+  b.job[0].soft = soft;
   b.work = mv.ctr + kCtrWork;
   return launch_direct_batch(b, st);
 }

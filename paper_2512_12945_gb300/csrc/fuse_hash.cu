@@ -429,6 +429,7 @@ cudaError_t launch_fuse_hash(const MapView& mv, const ScanGeom& g, const float* 
   b.job[0].K = K;
   b.job[0].band_blocks = band_blocks;
   b.job[0].latest = 0;
+  b.job[0].soft = 0;
   b.work = mv.ctr + kCtrWork;
   return launch_hash_batch(b, tile, 0, st);
 }

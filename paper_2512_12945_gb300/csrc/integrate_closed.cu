@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256, 2)
           const float a1 = __shfl_down_sync(0xFFFFFFFFu, pv, off);
           if ((int)lane + off <= lastl) pv += a1;
         }
-        if (r && (int)lane == first) atomicAdd(r + 2 + k, pv);
+        if (r && (int)lane == first) atomicAdd(r + kSoftCnt + k, pv);
       }
     }
   }

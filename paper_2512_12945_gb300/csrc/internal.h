@@ -26,6 +26,7 @@ struct HashJob {
   int32_t K;
   int32_t band_blocks;
   int32_t latest;       // latest-label mode (direct reductions only)
+  int32_t soft;         // soft counts (direct reductions)
   int32_t tile_points;  // set by launch_hash_batch
   uint32_t tile_begin;  // set by launch_hash_batch
 };
@@ -40,7 +41,8 @@ cudaError_t launch_hash_batch(HashBatch& b, int tile, int ctas_per_sm, cudaStrea
 cudaError_t hash_setup_attributes();
 // Direct per-pair reductions, one scan / the jobs of b in one grid.
 cudaError_t launch_fuse_direct(const MapView& mv, const ScanGeom& g, const float* pts,
-                               const float* sem, int64_t n, int K, int latest, cudaStream_t st);
+                               const float* sem, int64_t n, int K, int latest, int soft,
+                               cudaStream_t st);
 cudaError_t launch_direct_batch(HashBatch& b, cudaStream_t st);
 // Zero the records of the blocks allocated so far (closed-set maps).
 cudaError_t launch_zero_used_blocks(const MapView& mv, cudaStream_t st);

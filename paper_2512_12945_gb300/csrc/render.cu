@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_render(const __grid_constant__ RenderAr
         } else if (!a.open) {
           const size_t vox = (size_t)slot * kBlockVoxels + local_index(ry.i0, ry.i1, ry.i2);
           const float* r = mv.rec + vox * mv.rs;
-          const float* cnt = mv.split ? r + 1 : r + 2;
+          const float* cnt = mv.split ? r + 1 : r + kSoftCnt;
           const int cs = mv.split ? 2 : 1;
           lab = 0;
           float bv = cnt[0];
