@@ -58,6 +58,8 @@ def parse():
                     default="street", help="street (default, the headline line) or a "
                     "secondary configuration, each printing its own JSON line")
     ap.add_argument("--frames", type=int, default=4, help="indoor: RGB-D frames per step")
+    ap.add_argument("--voxel-capacity", type=int, default=2_000_000,
+                    help="indoor: voxel rows reserved per map")
     ap.add_argument("--block-capacity", type=int, default=65536,
                     help="street: 8^3 blocks reserved per map (100 scans use ~26k)")
     return ap.parse_args()
@@ -200,7 +202,7 @@ def strategy(tile):
 def kernel_source_sha(src="fuse_direct.cu"):
     """Hash of the sources of the dominant kernel."""
     h = hashlib.sha256()
-    for f in (src, "closed_common.cuh", "common.cuh", "geometry.cuh", "hash.cuh"):
+    for f in (src, "closed_common.cuh", "common.cuh", "geometry.cuh", "hash.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_2512_12945_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -614,7 +616,7 @@ def run_indoor(args):
         m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, mode="open", embed_dim=512,
                      embed_storage=storage, min_range=w.min_range, max_range=w.max_range,
                      max_points=640 * 480, block_capacity=200000, hash_capacity=1 << 20,
-                     voxel_capacity=2_000_000)
+                     voxel_capacity=args.voxel_capacity)
 
         def step():
             m.reset()

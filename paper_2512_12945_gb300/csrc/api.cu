@@ -489,7 +489,7 @@ slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
     if ((s = slim_map_reset(m, stream)) != SLIM_OK) break;
     const int tile = cand[c];
     auto launch = [&]() {
-      return tile == 0 ? launch_direct_batch(b, st) : launch_hash_batch(b, tile, 0, st);
+      return tile == 0 ? launch_direct_batch(b, 0, st) : launch_hash_batch(b, tile, 0, st);
     };
     cudaError_t e = cudaSuccess;
     for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch();
@@ -737,16 +737,16 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
     b.n_jobs = 0;
     return e == cudaSuccess ? SLIM_OK : cuda_fail(e, "launch_hash_batch");
   };
-  // direct-reduction maps share one grid per 16 scans
-  HashBatch nb;
-  nb.n_jobs = 0;
-  slim_map* direct0 = nullptr;
-  auto flush_direct = [&]() -> slim_status {
-    if (nb.n_jobs == 0) return SLIM_OK;
-    const int tok = prof_begin(direct0, SLIM_KERNEL_BATCH, st);
-    cudaError_t e = launch_direct_batch(nb, st);
-    prof_end(direct0, tok, st);
-    nb.n_jobs = 0;
+  // direct-reduction maps share one grid per 16 scans and mode
+  HashBatch nb[3];
+  slim_map* direct0[3] = {nullptr, nullptr, nullptr};
+  for (int q = 0; q < 3; ++q) nb[q].n_jobs = 0;
+  auto flush_direct = [&](int q) -> slim_status {
+    if (nb[q].n_jobs == 0) return SLIM_OK;
+    const int tok = prof_begin(direct0[q], SLIM_KERNEL_BATCH, st);
+    cudaError_t e = launch_direct_batch(nb[q], q, st);
+    prof_end(direct0[q], tok, st);
+    nb[q].n_jobs = 0;
     return e == cudaSuccess ? SLIM_OK : cuda_fail(e, "launch_direct_batch");
   };
   for (int32_t k = 0; k < n_items; ++k) {
@@ -755,8 +755,9 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
     m->scans++;
     if (it.n == 0) continue;
     if (uses_direct(m)) {
-      if (!direct0) direct0 = m;
-      HashJob& J = nb.job[nb.n_jobs++];
+      const int q = m->mode == SLIM_CLOSED_SOFT ? 1 : (m->mode == SLIM_CLOSED_LATEST ? 2 : 0);
+      if (!direct0[q]) direct0[q] = m;
+      HashJob& J = nb[q].job[nb[q].n_jobs++];
       compose_pose(it.pose, m->p.body_from_sensor, J.g, m->p.voxel_size, m->p.trunc,
                    m->p.min_range, m->p.max_range, m->cap);
       J.g.scan_no = (uint32_t)m->scans;
@@ -768,8 +769,8 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
       J.band_blocks = m->band_blocks;
       J.latest = m->mode == SLIM_CLOSED_LATEST ? 1 : 0;
       J.soft = m->mode == SLIM_CLOSED_SOFT ? 1 : 0;
-      if (nb.n_jobs == kMaxHashJobs) {
-        slim_status s = flush_direct();
+      if (nb[q].n_jobs == kMaxHashJobs) {
+        slim_status s = flush_direct(q);
         if (s != SLIM_OK) return s;
       }
     } else if (uses_hash(m)) {
@@ -799,8 +800,10 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
       if (s != SLIM_OK) return s;
     }
   }
-  slim_status s = flush_direct();
-  if (s != SLIM_OK) return s;
+  for (int q = 0; q < 3; ++q) {
+    slim_status s = flush_direct(q);
+    if (s != SLIM_OK) return s;
+  }
   return flush();
 }
 

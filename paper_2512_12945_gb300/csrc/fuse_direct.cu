@@ -78,6 +78,9 @@ __device__ __forceinline__ uint32_t map_block_slot(const MapView& mv, uint64_t k
   return kFailSlot;
 }
 
+// MODE: 0 one-hot, 1 soft counts, 2 latest label (every job of a launch
+// has the launch's mode, so the per-pair loop carries no mode branch).
+template <int MODE>
 __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_constant__ HashBatch b) {
   const uint32_t t = blockIdx.x;
   const HashJob& J = b.job[job_of(b, t)];
@@ -87,18 +90,15 @@ __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_con
   if (j >= J.n) return;
   Ray ry;
   if (!ray_setup_at(J.g, J.pts, j, ry)) return;
-  const uint32_t cls = J.soft ? 0u : argmax_row(J.sem + (size_t)j * J.K, J.K);
+  const uint32_t cls = MODE == 1 ? 0u : argmax_row(J.sem + (size_t)j * J.K, J.K);
   uint32_t slot = kFailSlot;
-  const unsigned long long stamp = ((unsigned long long)J.g.scan_no << 40) |
-                                   ((unsigned long long)(uint32_t)j << 8) | cls;
   ray_for_each_blk(J.g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d, bool new_block) {
     if (new_block) slot = map_block_slot(mv, pack_block(i0 >> 3, i1 >> 3, i2 >> 3));
     if (slot >= mv.block_cap) return;
     float* r = mv.rec + ((size_t)slot * kBlockVoxels + local_index(i0, i1, i2)) * mv.rs;
-    if (J.latest) {
-      red_add_v2(r, d, 1.f);
-      atomicMax(reinterpret_cast<unsigned long long*>(r + 2), stamp);
-    } else if (J.soft) {
+    if (MODE == 0) {
+      red_add_v2(r + 2 * cls, d, 1.f);
+    } else if (MODE == 1) {
       // soft counts: (S, W) += (d, 1) and c += p, four classes per reduction
       red_add_v2(r, d, 1.f);
       const float* p = J.sem + (size_t)j * J.K;
@@ -110,12 +110,16 @@ __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_con
         red_add_v4(r + kSoftCnt + k, a0, a1, a2, a3);
       }
     } else {
-      red_add_v2(r + 2 * cls, d, 1.f);
+      const unsigned long long stamp = ((unsigned long long)J.g.scan_no << 40) |
+                                       ((unsigned long long)(uint32_t)j << 8) | cls;
+      red_add_v2(r, d, 1.f);
+      atomicMax(reinterpret_cast<unsigned long long*>(r + 2), stamp);
     }
   });
 }
 
-cudaError_t launch_direct_batch(HashBatch& b, cudaStream_t st) {
+// All jobs of b share one mode (0 one-hot, 1 soft, 2 latest).
+cudaError_t launch_direct_batch(HashBatch& b, int mode, cudaStream_t st) {
   uint32_t total = 0;
   for (int j = 0; j < b.n_jobs; ++j) {
     b.job[j].tile_points = kDirectThreads;
@@ -124,7 +128,12 @@ cudaError_t launch_direct_batch(HashBatch& b, cudaStream_t st) {
   }
   b.total_tiles = total;
   if (total == 0) return cudaSuccess;
-  k_fuse_direct<<<total, kDirectThreads, 0, st>>>(b);
+  if (mode == 1)
+    k_fuse_direct<1><<<total, kDirectThreads, 0, st>>>(b);
+  else if (mode == 2)
+    k_fuse_direct<2><<<total, kDirectThreads, 0, st>>>(b);
+  else
+    k_fuse_direct<0><<<total, kDirectThreads, 0, st>>>(b);
   return cudaGetLastError();
 }
 
@@ -144,7 +153,7 @@ cudaError_t launch_fuse_direct(const MapView& mv, const ScanGeom& g, const float
   b.job[0].latest = latest;
   b.job[0].soft = soft;
   b.work = mv.ctr + kCtrWork;
-  return launch_direct_batch(b, st);
+  return launch_direct_batch(b, soft ? 1 : (latest ? 2 : 0), st);
 }
 
 }  // namespace slim

@@ -43,7 +43,7 @@ cudaError_t hash_setup_attributes();
 cudaError_t launch_fuse_direct(const MapView& mv, const ScanGeom& g, const float* pts,
                                const float* sem, int64_t n, int K, int latest, int soft,
                                cudaStream_t st);
-cudaError_t launch_direct_batch(HashBatch& b, cudaStream_t st);
+cudaError_t launch_direct_batch(HashBatch& b, int mode, cudaStream_t st);
 // Zero the records of the blocks allocated so far (closed-set maps).
 cudaError_t launch_zero_used_blocks(const MapView& mv, cudaStream_t st);
 cudaError_t launch_fuse_hash(const MapView& mv, const ScanGeom& g, const float* pts,
