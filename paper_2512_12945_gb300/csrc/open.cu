@@ -175,47 +175,71 @@ __device__ __forceinline__ float4 sem4(const float* __restrict__ sem, uint32_t p
             : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Batch mean and M2 of one fragment [fb, fe) for elements [e, e + 4),
-// accumulated about the fragment's first observation (S1 = sum (z - s),
-// S2 = sum (z - s)^2, mean = s + S1 / n, M2 = S2 - S1^2 / n).
-__device__ __forceinline__ void frag_stats(const float* __restrict__ sem, int L, uint32_t pt0,
-                                           uint32_t pt1, int fb, int fe, int e, bool on,
-                                           float mean[4], float m2[4]) {
-  const float4 s4 = sem4(sem, piece_pt(pt0, pt1, fb), L, e, on);
-  const float sh[4] = {s4.x, s4.y, s4.z, s4.w};
-  float s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
+// Batch mean and M2 of one fragment [fb, fe) for G groups of 4 elements
+// (e[g] = the lane's first element of group g), accumulated about the
+// fragment's first observation s (S1 = sum (z - s), S2 = sum (z - s)^2,
+// mean = s + S1 / n, M2 = S2 - S1^2 / n): one walk over the observations,
+// G independent 16-byte loads per observation, two observations per step.
+template <int G>
+__device__ __forceinline__ void frag_stats_g(const float* __restrict__ sem, int L, uint32_t pt0,
+                                             uint32_t pt1, int fb, int fe, const int (&e)[G],
+                                             const bool (&on)[G], float (&mean)[G][4],
+                                             float (&m2)[G][4]) {
+  float sh[G][4], s1[G][4], s2[G][4];
+  {
+    const uint32_t pf = piece_pt(pt0, pt1, fb);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const float4 v = sem4(sem, pf, L, e[g], on[g]);
+      sh[g][0] = v.x; sh[g][1] = v.y; sh[g][2] = v.z; sh[g][3] = v.w;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s1[g][q] = s2[g][q] = 0.f;
+    }
+  }
   int k = fb + 1;
-  for (; k + 3 < fe; k += 4) {
-    float4 z[4];
+  for (; k + 1 < fe; k += 2) {
+    const uint32_t pa = piece_pt(pt0, pt1, k), pb = piece_pt(pt0, pt1, k + 1);
+    float4 za[G], zb[G];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) z[u] = sem4(sem, piece_pt(pt0, pt1, k + u), L, e, on);
+    for (int g = 0; g < G; ++g) {
+      za[g] = sem4(sem, pa, L, e[g], on[g]);
+      zb[g] = sem4(sem, pb, L, e[g], on[g]);
+    }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const float zv[4] = {z[u].x, z[u].y, z[u].z, z[u].w};
+    for (int g = 0; g < G; ++g) {
+      const float va[4] = {za[g].x, za[g].y, za[g].z, za[g].w};
+      const float vb[4] = {zb[g].x, zb[g].y, zb[g].z, zb[g].w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float y = __fsub_rn(zv[q], sh[q]);
-        s1[q] = __fadd_rn(s1[q], y);
-        s2[q] = __fadd_rn(s2[q], __fmul_rn(y, y));
+        const float ya = __fsub_rn(va[q], sh[g][q]);
+        const float yb = __fsub_rn(vb[q], sh[g][q]);
+        s1[g][q] = __fadd_rn(s1[g][q], __fadd_rn(ya, yb));
+        s2[g][q] = __fadd_rn(s2[g][q], __fadd_rn(__fmul_rn(ya, ya), __fmul_rn(yb, yb)));
       }
     }
   }
-  for (; k < fe; ++k) {
-    const float4 z = sem4(sem, piece_pt(pt0, pt1, k), L, e, on);
-    const float zv[4] = {z.x, z.y, z.z, z.w};
+  if (k < fe) {
+    const uint32_t pa = piece_pt(pt0, pt1, k);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float y = __fsub_rn(zv[q], sh[q]);
-      s1[q] = __fadd_rn(s1[q], y);
-      s2[q] = __fadd_rn(s2[q], __fmul_rn(y, y));
+    for (int g = 0; g < G; ++g) {
+      const float4 z = sem4(sem, pa, L, e[g], on[g]);
+      const float va[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float ya = __fsub_rn(va[q], sh[g][q]);
+        s1[g][q] = __fadd_rn(s1[g][q], ya);
+        s2[g][q] = __fadd_rn(s2[g][q], __fmul_rn(ya, ya));
+      }
     }
   }
   const float invn = __fdiv_rn(1.0f, (float)(fe - fb));
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    mean[q] = __fadd_rn(sh[q], __fmul_rn(s1[q], invn));
-    m2[q] = fmaxf(__fsub_rn(s2[q], __fmul_rn(__fmul_rn(s1[q], s1[q]), invn)), 0.f);
-  }
+  for (int g = 0; g < G; ++g)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      mean[g][q] = __fadd_rn(sh[g][q], __fmul_rn(s1[g][q], invn));
+      m2[g][q] = fmaxf(__fsub_rn(s2[g][q], __fmul_rn(__fmul_rn(s1[g][q], s1[g][q]), invn)), 0.f);
+    }
 }
 
 // Voxel row of key (slot << 9 | local), allocated on its first observation
@@ -332,12 +356,19 @@ __global__ void __launch_bounds__(256) k_open_frag(MapView mv, const uint32_t* _
         const float fm = (float)nf / Wn, fbw = sw.y * (float)nf / Wn;
         const size_t rbase = (size_t)row * L;
         float nrm = 0.f;
-        for (int c0 = 0; c0 < L; c0 += 128) {
-          const int e = c0 + 4 * (int)lane;
-          const bool on = e < L;
-          float mean[4], m2[4];
-          frag_stats(sem, L, pt0, pt1, fb, fe, e, on, mean, m2);
-          if (on) nrm += nig_apply4<BF16>(mv, rbase, e, fresh, fm, fbw, mean, m2);
+        for (int c0 = 0; c0 < L; c0 += 512) {
+          int e[4];
+          bool on[4];
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            e[g] = c0 + 128 * g + 4 * (int)lane;
+            on[g] = e[g] < L;
+          }
+          float mean[4][4], m2[4][4];
+          frag_stats_g<4>(sem, L, pt0, pt1, fb, fe, e, on, mean, m2);
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            if (on[g]) nrm += nig_apply4<BF16>(mv, rbase, e[g], fresh, fm, fbw, mean[g], m2[g]);
         }
         nrm = warp_sum(nrm);
         if (lane == 0) {
@@ -350,16 +381,23 @@ __global__ void __launch_bounds__(256) k_open_frag(MapView mv, const uint32_t* _
       const uint32_t flags = kFragValid | (before ? 0u : (uint32_t)kFragHead) |
                              (after ? 0u : (uint32_t)kFragEnd);
       float2* dst = part + (size_t)(2 * p + side) * L;
-      for (int c0 = 0; c0 < L; c0 += 128) {
-        const int e = c0 + 4 * (int)lane;
-        const bool on = e < L;
-        float mean[4], m2[4];
-        frag_stats(sem, L, pt0, pt1, fb, fe, e, on, mean, m2);
-        if (on) {
-          float4* d4 = reinterpret_cast<float4*>(dst + e);
-          d4[0] = make_float4(mean[0], m2[0], mean[1], m2[1]);
-          d4[1] = make_float4(mean[2], m2[2], mean[3], m2[3]);
+      for (int c0 = 0; c0 < L; c0 += 512) {
+        int e[4];
+        bool on[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          e[g] = c0 + 128 * g + 4 * (int)lane;
+          on[g] = e[g] < L;
         }
+        float mean[4][4], m2[4][4];
+        frag_stats_g<4>(sem, L, pt0, pt1, fb, fe, e, on, mean, m2);
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+          if (on[g]) {
+            float4* d4 = reinterpret_cast<float4*>(dst + e[g]);
+            d4[0] = make_float4(mean[g][0], m2[g][0], mean[g][1], m2[g][1]);
+            d4[1] = make_float4(mean[g][2], m2[g][2], mean[g][3], m2[g][3]);
+          }
       }
       if (lane == 0) meta[2 * p + side] = make_uint4((uint32_t)nf, __float_as_uint(sd), flags, key);
     }
