@@ -407,9 +407,16 @@ __global__ void __launch_bounds__(256) k_open_frag(MapView mv, const uint32_t* _
 
 // One warp per run that leaves the piece it starts in: merge its fragments
 // (side 1 of the head piece, side 0 of the following pieces up to the
-// fragment flagged as the run's end) and apply the run.
+// fragment flagged as the run's end) and apply the run. A voxel close to
+// the sensor can collect thousands of observations in one frame, so a run
+// can span tens of pieces: the run's end is searched 32 pieces per step
+// (one piece metadata word per lane) and the fragments' statistics are
+// loaded kMergeAhead pieces at a time, so the warp's chain of dependent
+// loads grows with the run length / kMergeAhead, not with the run length.
+constexpr int kMergeAhead = 6;
+
 template <int BF16>
-__global__ void __launch_bounds__(256) k_open_merge(MapView mv, const uint32_t* __restrict__ ctr,
+__global__ void __launch_bounds__(256, 2) k_open_merge(MapView mv, const uint32_t* __restrict__ ctr,
                                                     int L, int64_t n_max,
                                                     const float2* __restrict__ part,
                                                     const uint4* __restrict__ meta) {
@@ -422,25 +429,32 @@ __global__ void __launch_bounds__(256) k_open_merge(MapView mv, const uint32_t* 
     const uint4 h = meta[2 * p + 1];
     if (!(h.z & kFragHead)) continue;
     const uint32_t key = h.w;
-    // the chain of pieces: count, sum d and its end
-    float ntot = (float)h.x, sd = __uint_as_float(h.y);
-    int64_t q = p + 1;
-    bool ok = false;
-    for (; q < np; ++q) {
-      const uint4 t = meta[2 * q];
-      if (!(t.z & kFragValid) || t.w != key) break;
-      ntot += (float)t.x;
-      sd += __uint_as_float(t.y);
-      if (t.z & kFragEnd) {
-        ok = true;
+    // the chain of pieces after p: count, sum d and the end piece
+    float ntot = 0.f, sd = 0.f;
+    int64_t q_end = -1;
+    for (int64_t b0 = p + 1; b0 < np; b0 += 32) {
+      const int64_t q = b0 + (int64_t)lane;
+      const uint4 t = q < np ? meta[2 * q] : make_uint4(0u, 0u, 0u, 0u);
+      const bool same = (t.z & kFragValid) && t.w == key;
+      const unsigned brk = __ballot_sync(0xFFFFFFFFu, !same);
+      const unsigned end = __ballot_sync(0xFFFFFFFFu, same && (t.z & kFragEnd));
+      const int nb = brk ? __ffs(brk) - 1 : 32;  // first lane outside the chain
+      const int ne = end ? __ffs(end) - 1 : 32;  // first lane holding the end
+      const int take = ne < nb ? ne + 1 : nb;
+      ntot += warp_sum((int)lane < take ? (float)t.x : 0.f);
+      sd += warp_sum((int)lane < take ? __uint_as_float(t.y) : 0.f);
+      if (ne < nb) {
+        q_end = b0 + ne;
         break;
       }
+      if (nb < 32) break;
     }
-    if (!ok) {  // consistency check, never expected
+    if (q_end < 0) {  // consistency check, never expected
       if (lane == 0) raise_status(mv.ctr, kDevInternal, 13);
       continue;
     }
-    const int64_t q_end = q;
+    ntot += (float)h.x;
+    sd += __uint_as_float(h.y);
     int fresh = 0;
     const int32_t row = voxel_row(mv, key, &fresh);
     if (row < 0) continue;
@@ -460,27 +474,42 @@ __global__ void __launch_bounds__(256) k_open_merge(MapView mv, const uint32_t* 
         mean[0] = a.x; m2[0] = a.y; mean[1] = a.z; m2[1] = a.w;
         mean[2] = b.x; m2[2] = b.y; mean[3] = b.z; m2[3] = b.w;
       }
-      for (int64_t r = p + 1; r <= q_end; ++r) {
-        const float nb = (float)meta[2 * r].x;
-        const float4* s4 = reinterpret_cast<const float4*>(part + (size_t)(2 * r) * L + e);
-        const float4 a = s4[0], b = s4[1];
-        const float mb[4] = {a.x, a.z, b.x, b.z}, vb[4] = {a.y, a.w, b.y, b.w};
-        const float nn = na + nb;
-        const float wb = nb / nn, wab = na * nb / nn;
+      for (int64_t r0 = p + 1; r0 <= q_end; r0 += kMergeAhead) {
+        float nbv[kMergeAhead];
+        float4 av[kMergeAhead], bv[kMergeAhead];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float dl = mb[u] - mean[u];
-          // mean += dl * nb / n and M2 += M2_b + dl^2 na nb / n, compensated
-          const float ym = __fsub_rn(__fmul_rn(dl, wb), mc[u]);
-          const float tm = __fadd_rn(mean[u], ym);
-          mc[u] = __fsub_rn(__fsub_rn(tm, mean[u]), ym);
-          mean[u] = tm;
-          const float yv = __fsub_rn(__fadd_rn(vb[u], __fmul_rn(__fmul_rn(dl, dl), wab)), vc[u]);
-          const float tv = __fadd_rn(m2[u], yv);
-          vc[u] = __fsub_rn(__fsub_rn(tv, m2[u]), yv);
-          m2[u] = tv;
+        for (int u = 0; u < kMergeAhead; ++u) {
+          const int64_t r = r0 + u;
+          if (r <= q_end) {
+            nbv[u] = (float)meta[2 * r].x;
+            const float4* s4 = reinterpret_cast<const float4*>(part + (size_t)(2 * r) * L + e);
+            av[u] = s4[0];
+            bv[u] = s4[1];
+          }
         }
-        na = nn;
+#pragma unroll
+        for (int u = 0; u < kMergeAhead; ++u) {
+          if (r0 + u > q_end) break;
+          const float nb = nbv[u];
+          const float mb[4] = {av[u].x, av[u].z, bv[u].x, bv[u].z};
+          const float vb[4] = {av[u].y, av[u].w, bv[u].y, bv[u].w};
+          const float nn = na + nb;
+          const float wb = nb / nn, wab = na * nb / nn;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float dl = mb[k] - mean[k];
+            // mean += dl * nb / n and M2 += M2_b + dl^2 na nb / n, compensated
+            const float ym = __fsub_rn(__fmul_rn(dl, wb), mc[k]);
+            const float tm = __fadd_rn(mean[k], ym);
+            mc[k] = __fsub_rn(__fsub_rn(tm, mean[k]), ym);
+            mean[k] = tm;
+            const float yv = __fsub_rn(__fadd_rn(vb[k], __fmul_rn(__fmul_rn(dl, dl), wab)), vc[k]);
+            const float tv = __fadd_rn(m2[k], yv);
+            vc[k] = __fsub_rn(__fsub_rn(tv, m2[k]), yv);
+            m2[k] = tv;
+          }
+          na = nn;
+        }
       }
       nrm += nig_apply4<BF16>(mv, rbase, e, fresh, fm, fbw, mean, m2);
     }
