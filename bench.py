@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "points integrated/s (TSDF+Bayes semantic), % HBM roofline, plain vs chosen"
 UNIT = "points/s"
 COUNTS = os.path.join(ROOT, "tests", "golden", "street_lidar_counts.json")
+INDOOR_COUNTS = os.path.join(ROOT, "tests", "golden", "indoor_rgbd_counts.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 K_CLASSES = 20
 
@@ -169,6 +170,24 @@ def measured_peak():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def open_algorithmic_bytes(n_frames, L, bf16):
+    """Open-set integration: B = N_all*12 + N_valid*4l + (2*U_old + U_new)*R
+    + U_b*16 per frame, R = 8 + 8l (FP32 mean and beta) or 8 + 4l (BF16), with
+    the counts of the oracle's pair generator; None when the stored counts
+    do not cover n_frames frames."""
+    try:
+        with open(INDOOR_COUNTS) as f:
+            rows = json.load(f)["scans"]
+    except (OSError, KeyError, ValueError):
+        return None
+    if len(rows) < n_frames:
+        return None
+    R = 8 + (4 if bf16 else 8) * L
+    return sum(r["points"] * 12 + r["valid"] * 4 * L +
+               (2 * (r["voxels"] - r["new_voxels"]) + r["new_voxels"]) * R + r["blocks"] * 16
+               for r in rows[:n_frames])
 
 
 def algorithmic_bytes(counts, n_scans):
@@ -650,8 +669,15 @@ def run_indoor(args):
         kq = qkms / max(nq, 1)
         flops = 2.0 * rows * 512 * 256
         peak, kind = _bf16_peak()
+        B = open_algorithmic_bytes(args.frames, 512, storage == "bf16")
+        hbm_peak, hbm_kind = measured_peak()
+        roof = None if B is None else {
+            "bound": "hbm", "achieved": round(B / (ms / 1e3) / 1e9, 1), "peak": hbm_peak,
+            "unit": "GB/s", "frac": round(B / (ms / 1e3) / 1e9 / hbm_peak, 4),
+            "peak_source": hbm_kind, "algorithmic_bytes_per_step": B,
+            "scope": "whole integration call per frame (traverse, pairs, sort, fragments, merge)"}
         out[storage] = {"points_per_s": valid * args.steps / (ms * args.steps / 1e3),
-                        "ms_per_step": ms, "voxels": rows,
+                        "ms_per_step": ms, "voxels": rows, "integrate_roofline": roof,
                         "depth_front_end": {"ms_per_step": dms,
                                             "points_per_s": valid / (dms / 1e3),
                                             "call": "slim_integrate_depth per frame"},
