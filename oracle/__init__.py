@@ -48,7 +48,8 @@ class _Params(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("num_classes", ctypes.c_int32),
                 ("embed_dim", ctypes.c_int32), ("fp64_geometry", ctypes.c_int32),
                 ("alpha0", ctypes.c_double),
-                ("body_from_sensor", ctypes.c_double * 16)]
+                ("body_from_sensor", ctypes.c_double * 16),
+                ("weighting", ctypes.c_int32), ("weight_eps", ctypes.c_float)]
 
 
 def _load():
@@ -109,7 +110,10 @@ def _pose(pose):
 
 def make_params(voxel_size, trunc, mode=CLOSED_ONEHOT, num_classes=0, embed_dim=0,
                 min_range=0.0, max_range=1e30, alpha0=1.0, fp64_geometry=False,
-                body_from_sensor=None):
+                body_from_sensor=None, weighting=0, weight_eps=0.0):
+    """weighting 0: w~ = 1 (Sec. III-A); 1: linear decay behind the surface
+    (w~ = 1 for d >= -weight_eps, (tau + d) / (tau - weight_eps) below),
+    closed-set modes only."""
     p = _Params()
     p.voxel_size = voxel_size
     p.trunc = trunc
@@ -120,6 +124,8 @@ def make_params(voxel_size, trunc, mode=CLOSED_ONEHOT, num_classes=0, embed_dim=
     p.embed_dim = embed_dim
     p.fp64_geometry = int(bool(fp64_geometry))
     p.alpha0 = alpha0
+    p.weighting = int(weighting)
+    p.weight_eps = float(weight_eps)
     ext = np.eye(4) if body_from_sensor is None else np.asarray(body_from_sensor, np.float64)
     for k, val in enumerate(ext.reshape(16)):
         p.body_from_sensor[k] = float(val)
@@ -137,6 +143,9 @@ class OracleMap:
         self.lib = _load()
         self.params = make_params(**kw)
         self.h = self.lib.ora_create(ctypes.byref(self.params))
+        if not self.h:
+            raise ValueError("unsupported oracle parameters (weighting applies to the closed "
+                             "set, with 0 <= weight_eps < trunc)")
         self.w = sem_width(self.params)
 
     def __del__(self):
@@ -217,6 +226,8 @@ class OracleMap:
         gxyz = np.zeros((n, 3))
         rc = self.lib.ora_backward_scan(self.h, _ptr(pts), n, _ptr(pose), _ptr(sem), _ptr(gD),
                                         _ptr(gS), _ptr(gB), _ptr(gsem), _ptr(gxyz))
+        if rc == -2:
+            raise RuntimeError("ora_backward_scan: the adjoint is for w~ = 1 maps")
         if rc != 0:
             raise RuntimeError("ora_backward_scan: extract() must be called first")
         return gsem, gxyz

@@ -55,6 +55,8 @@ struct Params {
   int32_t fp64_geometry;
   double alpha0;
   double body_from_sensor[16];  // row-major 4x4
+  int32_t weighting;  // 0: w~ = 1; 1: linear decay behind the surface
+  float weight_eps;   // linear decay: w~ = 1 for d >= -eps (0 <= eps < tau)
 };
 
 struct VKey {
@@ -306,19 +308,31 @@ int argmax_first(const float* p, int K) {
   return best;
 }
 
+// The weight w~ of an observation with SDF d (Sec. III-A leaves the weighting
+// function open and names w~ = 1 as the common choice). weighting = 1 is the
+// linear decay behind the surface of Bylow et al. (RSS 2013), in this
+// code's sign convention (d > 0 in front of the surface): w~ = 1 for
+// d >= -eps, falling linearly to 0 at d = -tau.
+double obs_weight(const Params& P, double d) {
+  if (P.weighting == 0 || d >= -(double)P.weight_eps) return 1.0;
+  return ((double)P.trunc + d) / ((double)P.trunc - (double)P.weight_eps);
+}
+
 // Fuse one observation (d, semantic measurement) into a voxel.
 void fuse(const Params& P, Rec& rec, double d, const float* s) {
   const double W_prev = rec.W;
-  // Sec. III-A, w~ = 1: W_t = W_{t-1} + 1, D_t = (W_{t-1} D_{t-1} + d) / W_t.
-  rec.W = W_prev + 1.0;
-  rec.D = (W_prev * rec.D + d) / rec.W;
+  // Sec. III-A: W_t = W_{t-1} + w~, D_t = (W_{t-1} D_{t-1} + w~ d) / W_t.
+  const double wt = obs_weight(P, d);
+  rec.W = W_prev + wt;
+  rec.D = (W_prev * rec.D + wt * d) / rec.W;
   if (P.mode == CLOSED_ONEHOT) {
     // Theorem 1, Eq. (alpha_update): alpha_i += 1{z = i}, z = argmax of the
-    // network's class probabilities (one-hot prediction).
-    rec.sem[argmax_first(s, P.num_classes)] += 1.0;
+    // network's class probabilities (one-hot prediction); a weighted
+    // observation adds w~ (w~ = 1 is the paper's update).
+    rec.sem[argmax_first(s, P.num_classes)] += wt;
   } else if (P.mode == CLOSED_SOFT) {
-    // Soft-count reading of Eq. (alpha_update): alpha_i += p_i.
-    for (int k = 0; k < P.num_classes; ++k) rec.sem[k] += (double)s[k];
+    // Soft-count reading of Eq. (alpha_update): alpha_i += w~ p_i.
+    for (int k = 0; k < P.num_classes; ++k) rec.sem[k] += wt * (double)s[k];
   } else if (P.mode == CLOSED_LATEST) {
     // The non-Bayesian ablation of the evaluation (SLIM-VDB*): the voxel
     // keeps the most recent measurement's label, as a one-hot vector.
@@ -353,7 +367,13 @@ extern "C" {
 
 typedef Params ora_params;
 
+// Returns null for an unsupported combination: a weighting other than
+// w~ = 1 applies to the closed-set modes only (the open-set update ties the
+// NIG lambda to W, Sec. III-D).
 void* ora_create(const ora_params* p) {
+  if (p->weighting != 0 && (p->mode == OPEN || p->weighting != 1 ||
+                            !(p->weight_eps >= 0.0f && p->weight_eps < p->trunc)))
+    return nullptr;
   Map* m = new Map();
   m->p = *p;
   return m;
@@ -381,6 +401,9 @@ int64_t ora_integrate(void* h, const float* pts, int64_t n, const double pose[16
     ++valid;
     const float* s = sem + (size_t)j * (size_t)w;
     for (const Pair& pr : pairs) {
+      // an observation of weight 0 (d = -tau under the linear decay) changes
+      // nothing: a voxel is in the map once its weight W is positive
+      if (obs_weight(P, pr.d) == 0.0) continue;
       VKey key{pr.i[0], pr.i[1], pr.i[2]};
       auto it = m.vox.find(key);
       if (it == m.vox.end()) {
@@ -770,7 +793,7 @@ void ora_query(const double* rows, int64_t n, int32_t l, const float* q, int32_t
 }
 
 // Reverse-mode gradient of a loss L with respect to one scan's inputs, for a
-// map integrated from empty (so the final state is the batch posterior of all
+// map with w~ = 1 integrated from empty (so the final state is the batch posterior of all
 // observations, Theorems 1-2 with zero priors). Inputs are the loss
 // gradients per allocated voxel, in ora_extract order:
 //   gD (n_vox), gS (n_vox x w: dL/dc for closed SOFT, dL/dm for open),
@@ -790,6 +813,7 @@ int64_t ora_backward_scan(void* h, const float* pts, int64_t n, const double pos
   Map& m = *(Map*)h;
   const Params& P = m.p;
   if (m.order.size() != m.vox.size()) return -1;  // call ora_extract first
+  if (P.weighting != 0) return -2;                // the adjoint is for w~ = 1
   std::unordered_map<VKey, int64_t, VKeyHash> index;
   for (size_t j = 0; j < m.order.size(); ++j) index[m.order[j]] = (int64_t)j;
   float R[9], t[3];

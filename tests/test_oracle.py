@@ -730,3 +730,76 @@ def test_integrate_depth_backprojection():
     assert len(e["W"]) > 0 and (e["ijk"][:, :2] == 0).all()
     np.testing.assert_allclose(e["D"], np.clip(1.0 - (e["ijk"][:, 2] + 0.5) * 0.1, -0.3, 0.3),
                                atol=1e-6)
+
+
+# ------------------------------------------------------- weighting w~ != 1
+def test_weighting_linear_axis_ray():
+    """A ray along +x with the linear behind-surface weighting: each band
+    voxel's d is x_0 - c (the axis-ray closed form); voxels in front of
+    -eps keep weight 1, those behind carry (tau + d) / (tau - eps), falling
+    to 0 at d = -tau, where the voxel stays out of the map."""
+    eps = V
+    o = _pose_t(0.05, 0.05, 0.05)
+    for r in [1.3337, 2.71, 7.77]:
+        m = oracle.OracleMap(voxel_size=V, trunc=TAU, num_classes=3, weighting=1,
+                             weight_eps=eps)
+        m.integrate([[r, 0, 0]], o, _onehot_probs(np.array([2]), 3))
+        e = m.extract()
+        x0 = 0.05 + r
+        c = (e["ijk"][:, 0] + 0.5) * V
+        d = np.minimum(x0 - c, TAU)
+        w = np.where(d >= -eps, 1.0, (TAU + d) / (TAU - eps))
+        np.testing.assert_allclose(e["W"], w, atol=1e-5)
+        assert (e["W"] > 0).all() and (e["W"] <= 1).all()
+        np.testing.assert_allclose(e["D"], d, atol=2e-6)  # one observation: D = d
+        np.testing.assert_allclose(e["sem"][:, 2], e["W"], rtol=1e-15)
+        # weights never increase with depth along the ray
+        assert (np.diff(e["W"][np.argsort(c)]) <= 1e-12).all()
+
+
+def test_weighting_keeps_front_voxels_and_sums():
+    """Invariants against the w~ = 1 map of the same scans: a voxel all of
+    whose observations lie in front of -eps is unchanged; every other voxel
+    has a smaller W; one-hot and soft counts still sum to W."""
+    w = synth.room_lidar(n_scans=3, n_beams=8, n_az=96)
+    eps = 0.5 * V
+    kw = dict(voxel_size=V, trunc=TAU, num_classes=10, min_range=0.1, max_range=100.0)
+    maps = {}
+    for mode in (oracle.CLOSED_ONEHOT, oracle.CLOSED_SOFT):
+        for wt in (0, 1):
+            m = oracle.OracleMap(mode=mode, weighting=wt, weight_eps=eps, **kw)
+            for s in w.scans:
+                m.integrate(s["pts"], s["pose"], s["sem"])
+            maps[mode, wt] = m.extract()
+    obs = _groupby_pairs(oracle.make_params(**kw), w.scans)
+    for mode in (oracle.CLOSED_ONEHOT, oracle.CLOSED_SOFT):
+        u, g = maps[mode, 0], maps[mode, 1]
+        gi = {tuple(k): i for i, k in enumerate(g["ijk"].tolist())}
+        front = 0
+        for k, key in enumerate(map(tuple, u["ijk"].tolist())):
+            dmin = min(x[2] for x in obs[key])
+            if dmin >= -eps:
+                front += 1
+                i = gi[key]
+                assert g["W"][i] == u["W"][k] and g["D"][i] == u["D"][k]
+                assert np.array_equal(g["sem"][i], u["sem"][k])
+            elif key in gi:
+                assert g["W"][gi[key]] < u["W"][k]
+        assert front > 0
+        np.testing.assert_allclose(g["sem"].sum(axis=1), g["W"], rtol=1e-6)
+
+
+def test_weighting_refused_for_open_set_and_adjoint():
+    with pytest.raises(ValueError):
+        oracle.OracleMap(voxel_size=V, trunc=TAU, mode=oracle.OPEN, embed_dim=8, weighting=1,
+                         weight_eps=0.05)
+    with pytest.raises(ValueError):
+        oracle.OracleMap(voxel_size=V, trunc=TAU, num_classes=3, weighting=1, weight_eps=TAU)
+    m = oracle.OracleMap(voxel_size=V, trunc=TAU, mode=oracle.CLOSED_SOFT, num_classes=3,
+                         weighting=1, weight_eps=0.05)
+    p = np.array([[1.0, 0.2, 0.1]], np.float32)
+    s = np.array([[0.2, 0.3, 0.5]], np.float32)
+    m.integrate(p, _pose_t(0, 0, 0), s)
+    e = m.extract()
+    with pytest.raises(RuntimeError):
+        m.backward_scan(p, _pose_t(0, 0, 0), s, np.zeros(len(e["W"])), np.zeros((len(e["W"]), 3)))
