@@ -91,6 +91,21 @@ typedef enum {
   SLIM_AGG_DIRECT = 3
 } slim_aggregation;
 
+/* Per-observation weight w~ of the TSDF update (Sec. III-A: W_t = W_{t-1} +
+ * w~, D_t = (W_{t-1} D_{t-1} + w~ d) / W_t; the paper uses w~ = 1):
+ *   SLIM_WEIGHT_CONSTANT  w~ = 1 (default);
+ *   SLIM_WEIGHT_LINEAR    the linear decay behind the surface of Bylow et
+ *                         al. (RSS 2013): w~ = 1 for d >= -weight_eps,
+ *                         (tau + d) / (tau - weight_eps) below, 0 at d = -tau
+ *                         (d > 0 in front of the surface). The class counts
+ *                         take the same weight (one-hot: c_z += w~; soft:
+ *                         c += w~ p), so sum c = W still holds; an
+ *                         observation of weight 0 changes nothing.
+ * The linear weighting serves the closed-set modes with direct reductions
+ * (aggregation AUTO or DIRECT); it has no adjoint (slim_backward returns
+ * SLIM_ERR_UNSUPPORTED). */
+typedef enum { SLIM_WEIGHT_CONSTANT = 0, SLIM_WEIGHT_LINEAR = 1 } slim_weighting;
+
 typedef struct {
   float voxel_size;      /* metres, > 0 */
   float trunc;           /* truncation tau in metres, 0 < tau <= 4 voxel_size */
@@ -109,6 +124,8 @@ typedef struct {
   int32_t aggregation;     /* slim_aggregation: how pairs reach the records */
   int32_t tile_points;     /* hash aggregation: points per CTA tile, 64, 128 or
                               256 (0 = 256); see slim_autotune */
+  int32_t weighting;       /* slim_weighting (default SLIM_WEIGHT_CONSTANT) */
+  float weight_eps;        /* SLIM_WEIGHT_LINEAR: metres, 0 <= eps < trunc */
 } slim_map_params;
 
 typedef struct slim_map slim_map;

@@ -68,7 +68,7 @@ namespace {
 int sem_width(const slim_map* m) { return m->mode == SLIM_OPEN ? m->L : m->K; }
 
 void compose_pose(const double pose[16], const double ext[16], ScanGeom& g, float v, float tau,
-                  float rmin, float rmax, int cap) {
+                  float rmin, float rmax, int cap, int weighting, float weight_eps) {
   double M[16];
   for (int r = 0; r < 4; ++r)
     for (int c = 0; c < 4; ++c) {
@@ -92,6 +92,8 @@ void compose_pose(const double pose[16], const double ext[16], ScanGeom& g, floa
   g.dw = 0;
   g.fx = g.fy = 1.f;
   g.cx = g.cy = 0.f;
+  g.weighting = weighting;
+  g.weight_eps = weight_eps;
 }
 
 bool finite_pose(const double* p) {
@@ -156,6 +158,16 @@ slim_status check_params(const slim_map_params* p) {
   if (p->mode == SLIM_CLOSED_LATEST && p->aggregation != SLIM_AGG_AUTO &&
       p->aggregation != SLIM_AGG_DIRECT)
     return fail(SLIM_ERR_ARG, "the latest-label mode uses direct reductions only");
+  if (p->weighting != SLIM_WEIGHT_CONSTANT && p->weighting != SLIM_WEIGHT_LINEAR)
+    return fail(SLIM_ERR_ARG, "weighting must be 0 (constant) or 1 (linear)");
+  if (p->weighting == SLIM_WEIGHT_LINEAR) {
+    if (p->mode == SLIM_OPEN)
+      return fail(SLIM_ERR_ARG, "the linear weighting serves the closed-set modes");
+    if (p->aggregation != SLIM_AGG_AUTO && p->aggregation != SLIM_AGG_DIRECT)
+      return fail(SLIM_ERR_ARG, "the linear weighting uses direct reductions");
+    if (!(p->weight_eps >= 0.f) || !(p->weight_eps < p->trunc))
+      return fail(SLIM_ERR_ARG, "weight_eps must be in [0, trunc)");
+  }
   return SLIM_OK;
 }
 
@@ -214,7 +226,7 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   }
   m->tile_points = closed_tile_points(m->cap, m->band_blocks);
   m->hash_tile = p->tile_points > 0 ? p->tile_points : 256;
-  m->direct = p->mode == SLIM_CLOSED_LATEST ||
+  m->direct = p->mode == SLIM_CLOSED_LATEST || p->weighting == SLIM_WEIGHT_LINEAR ||
               (p->mode == SLIM_CLOSED_SOFT &&
                (p->aggregation == SLIM_AGG_DIRECT || p->aggregation == SLIM_AGG_AUTO)) ||
               (p->mode == SLIM_CLOSED_ONEHOT &&
@@ -349,7 +361,8 @@ slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
   cudaStream_t st = (cudaStream_t)stream;
   ScanGeom g;
   compose_pose(pose_host, m->p.body_from_sensor, g, m->p.voxel_size, m->p.trunc,
-               m->p.min_range, m->p.max_range, m->cap);
+               m->p.min_range, m->p.max_range, m->cap, m->p.weighting,
+               m->p.weight_eps);
   m->scans++;
   g.scan_no = (uint32_t)m->scans;
   if (n == 0) return SLIM_OK;
@@ -393,7 +406,8 @@ slim_status slim_integrate_depth(slim_map* m, const float* depth_dev, int32_t wi
   cudaStream_t st = (cudaStream_t)stream;
   ScanGeom g;
   compose_pose(pose_host, m->p.body_from_sensor, g, m->p.voxel_size, m->p.trunc,
-               m->p.min_range, m->p.max_range, m->cap);
+               m->p.min_range, m->p.max_range, m->cap, m->p.weighting,
+               m->p.weight_eps);
   m->scans++;
   g.scan_no = (uint32_t)m->scans;
   g.depth = depth_dev;
@@ -452,7 +466,7 @@ slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
   int cand[4];
   int nc = 0;
   if (m->p.aggregation != SLIM_AGG_HASH) cand[nc++] = 0;
-  if (m->p.aggregation != SLIM_AGG_DIRECT) {
+  if (m->p.aggregation != SLIM_AGG_DIRECT && m->p.weighting == SLIM_WEIGHT_CONSTANT) {
     cand[nc++] = 64;
     cand[nc++] = 128;
     cand[nc++] = 256;
@@ -466,7 +480,8 @@ slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
   b.work = m->mv.ctr + kCtrWork;
   for (int k = 0; k < b.n_jobs; ++k) {
     compose_pose(pose_host, m->p.body_from_sensor, b.job[k].g, m->p.voxel_size, m->p.trunc,
-                 m->p.min_range, m->p.max_range, m->cap);
+                 m->p.min_range, m->p.max_range, m->cap, m->p.weighting,
+               m->p.weight_eps);
     b.job[k].mv = m->mv;
     b.job[k].pts = pts_dev;
     b.job[k].sem = static_cast<const float*>(sem_dev);
@@ -489,7 +504,8 @@ slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
     if ((s = slim_map_reset(m, stream)) != SLIM_OK) break;
     const int tile = cand[c];
     auto launch = [&]() {
-      return tile == 0 ? launch_direct_batch(b, 0, st) : launch_hash_batch(b, tile, 0, st);
+      return tile == 0 ? launch_direct_batch(b, m->p.weighting ? 3 : 0, st)
+                       : launch_hash_batch(b, tile, 0, st);
     };
     cudaError_t e = cudaSuccess;
     for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch();
@@ -692,11 +708,14 @@ slim_status slim_backward(slim_map* m, const float* pts_dev, int64_t n,
     return fail(SLIM_ERR_ARG, "pts, sem, gD, gsem and gxyz are required");
   if (m->mode == SLIM_CLOSED_LATEST)
     return fail(SLIM_ERR_UNSUPPORTED, "the latest-label mode has no adjoint");
+  if (m->p.weighting != SLIM_WEIGHT_CONSTANT)
+    return fail(SLIM_ERR_UNSUPPORTED, "the adjoint is for maps with w~ = 1");
   if (n > 0 && m->mode != SLIM_CLOSED_ONEHOT && !gS_dev)
     return fail(SLIM_ERR_ARG, "gS is required in the soft and open modes");
   ScanGeom g;
   compose_pose(pose_host, m->p.body_from_sensor, g, m->p.voxel_size, m->p.trunc,
-               m->p.min_range, m->p.max_range, m->cap);
+               m->p.min_range, m->p.max_range, m->cap, m->p.weighting,
+               m->p.weight_eps);
   return run_backward(m, g, pts_dev, static_cast<const float*>(sem_dev), n, gD_dev, gS_dev,
                       m->mode == SLIM_OPEN ? gB_dev : nullptr, gsem_dev, gxyz_dev,
                       (cudaStream_t)stream);
@@ -737,10 +756,10 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
     b.n_jobs = 0;
     return e == cudaSuccess ? SLIM_OK : cuda_fail(e, "launch_hash_batch");
   };
-  // direct-reduction maps share one grid per 16 scans and mode
-  HashBatch nb[3];
-  slim_map* direct0[3] = {nullptr, nullptr, nullptr};
-  for (int q = 0; q < 3; ++q) nb[q].n_jobs = 0;
+  // direct-reduction maps share one grid per 16 scans, mode and weighting
+  HashBatch nb[6];
+  slim_map* direct0[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  for (int q = 0; q < 6; ++q) nb[q].n_jobs = 0;
   auto flush_direct = [&](int q) -> slim_status {
     if (nb[q].n_jobs == 0) return SLIM_OK;
     const int tok = prof_begin(direct0[q], SLIM_KERNEL_BATCH, st);
@@ -755,11 +774,13 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
     m->scans++;
     if (it.n == 0) continue;
     if (uses_direct(m)) {
-      const int q = m->mode == SLIM_CLOSED_SOFT ? 1 : (m->mode == SLIM_CLOSED_LATEST ? 2 : 0);
+      const int q = (m->mode == SLIM_CLOSED_SOFT ? 1 : (m->mode == SLIM_CLOSED_LATEST ? 2 : 0)) +
+                    (m->p.weighting ? 3 : 0);
       if (!direct0[q]) direct0[q] = m;
       HashJob& J = nb[q].job[nb[q].n_jobs++];
       compose_pose(it.pose, m->p.body_from_sensor, J.g, m->p.voxel_size, m->p.trunc,
-                   m->p.min_range, m->p.max_range, m->cap);
+                   m->p.min_range, m->p.max_range, m->cap, m->p.weighting,
+               m->p.weight_eps);
       J.g.scan_no = (uint32_t)m->scans;
       J.mv = m->mv;
       J.pts = it.pts_dev;
@@ -780,7 +801,8 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
       }
       HashJob& J = b.job[b.n_jobs++];
       compose_pose(it.pose, m->p.body_from_sensor, J.g, m->p.voxel_size, m->p.trunc,
-                   m->p.min_range, m->p.max_range, m->cap);
+                   m->p.min_range, m->p.max_range, m->cap, m->p.weighting,
+               m->p.weight_eps);
       J.g.scan_no = (uint32_t)m->scans;
       J.latest = 0;
       J.soft = 0;
@@ -800,7 +822,7 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
       if (s != SLIM_OK) return s;
     }
   }
-  for (int q = 0; q < 3; ++q) {
+  for (int q = 0; q < 6; ++q) {
     slim_status s = flush_direct(q);
     if (s != SLIM_OK) return s;
   }

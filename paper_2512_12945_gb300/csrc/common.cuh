@@ -76,7 +76,18 @@ struct ScanGeom {
   const float* depth;
   int32_t dw;
   float fx, fy, cx, cy;
+  // per-observation weight w~ (Sec. III-A): 0 for w~ = 1, 1 for the linear
+  // decay behind the surface (closed-set maps, direct reductions)
+  int32_t weighting;
+  float weight_eps;
 };
+
+// w~ of an observation with SDF d under the linear decay behind the surface
+// (Bylow et al., RSS 2013; d > 0 in front of the surface here): 1 for
+// d >= -eps, (tau + d) / (tau - eps) below, 0 at d = -tau.
+__device__ __forceinline__ float obs_weight(const ScanGeom& g, float d) {
+  return d >= -g.weight_eps ? 1.f : __fdiv_rn(__fadd_rn(g.tau, d), __fsub_rn(g.tau, g.weight_eps));
+}
 
 // Block key: each block coordinate offset by 2^20 into 21 bits, x highest,
 // so the numeric order of keys is the lexicographic order of (bx, by, bz).

@@ -78,9 +78,11 @@ __device__ __forceinline__ uint32_t map_block_slot(const MapView& mv, uint64_t k
   return kFailSlot;
 }
 
-// MODE: 0 one-hot, 1 soft counts, 2 latest label (every job of a launch
-// has the launch's mode, so the per-pair loop carries no mode branch).
-template <int MODE>
+// MODE: 0 one-hot, 1 soft counts, 2 latest label; WT: observations carry
+// the weight w~ of the linear decay behind the surface instead of 1 (every
+// job of a launch has the launch's mode and weighting, so the per-pair loop
+// carries no branch on either).
+template <int MODE, bool WT>
 __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_constant__ HashBatch b) {
   const uint32_t t = blockIdx.x;
   const HashJob& J = b.job[job_of(b, t)];
@@ -95,30 +97,43 @@ __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_con
   ray_for_each_blk(J.g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d, bool new_block) {
     if (new_block) slot = map_block_slot(mv, pack_block(i0 >> 3, i1 >> 3, i2 >> 3));
     if (slot >= mv.block_cap) return;
+    // the observation adds (w~ d, w~); an observation of weight 0 changes
+    // nothing
+    const float wt = WT ? obs_weight(J.g, d) : 1.f;
+    if (WT && wt == 0.f) return;
+    const float wd = WT ? __fmul_rn(wt, d) : d;
     float* r = mv.rec + ((size_t)slot * kBlockVoxels + local_index(i0, i1, i2)) * mv.rs;
     if (MODE == 0) {
-      red_add_v2(r + 2 * cls, d, 1.f);
+      red_add_v2(r + 2 * cls, wd, wt);
     } else if (MODE == 1) {
-      // soft counts: (S, W) += (d, 1) and c += p, four classes per reduction
-      red_add_v2(r, d, 1.f);
+      // soft counts: (S, W) += (w~ d, w~) and c += w~ p, four classes per
+      // reduction
+      red_add_v2(r, wd, wt);
       const float* p = J.sem + (size_t)j * J.K;
       for (int k = 0; k < J.K; k += 4) {
-        const float a0 = __ldg(p + k);
-        const float a1 = k + 1 < J.K ? __ldg(p + k + 1) : 0.f;
-        const float a2 = k + 2 < J.K ? __ldg(p + k + 2) : 0.f;
-        const float a3 = k + 3 < J.K ? __ldg(p + k + 3) : 0.f;
+        float a0 = __ldg(p + k);
+        float a1 = k + 1 < J.K ? __ldg(p + k + 1) : 0.f;
+        float a2 = k + 2 < J.K ? __ldg(p + k + 2) : 0.f;
+        float a3 = k + 3 < J.K ? __ldg(p + k + 3) : 0.f;
+        if (WT) {
+          a0 = __fmul_rn(wt, a0);
+          a1 = __fmul_rn(wt, a1);
+          a2 = __fmul_rn(wt, a2);
+          a3 = __fmul_rn(wt, a3);
+        }
         red_add_v4(r + kSoftCnt + k, a0, a1, a2, a3);
       }
     } else {
       const unsigned long long stamp = ((unsigned long long)J.g.scan_no << 40) |
                                        ((unsigned long long)(uint32_t)j << 8) | cls;
-      red_add_v2(r, d, 1.f);
+      red_add_v2(r, wd, wt);
       atomicMax(reinterpret_cast<unsigned long long*>(r + 2), stamp);
     }
   });
 }
 
-// All jobs of b share one mode (0 one-hot, 1 soft, 2 latest).
+// All jobs of b share one variant: mode (0 one-hot, 1 soft, 2 latest) + 3
+// when the observations are weighted (linear decay).
 cudaError_t launch_direct_batch(HashBatch& b, int mode, cudaStream_t st) {
   uint32_t total = 0;
   for (int j = 0; j < b.n_jobs; ++j) {
@@ -128,12 +143,14 @@ cudaError_t launch_direct_batch(HashBatch& b, int mode, cudaStream_t st) {
   }
   b.total_tiles = total;
   if (total == 0) return cudaSuccess;
-  if (mode == 1)
-    k_fuse_direct<1><<<total, kDirectThreads, 0, st>>>(b);
-  else if (mode == 2)
-    k_fuse_direct<2><<<total, kDirectThreads, 0, st>>>(b);
-  else
-    k_fuse_direct<0><<<total, kDirectThreads, 0, st>>>(b);
+  switch (mode) {
+    case 1: k_fuse_direct<1, false><<<total, kDirectThreads, 0, st>>>(b); break;
+    case 2: k_fuse_direct<2, false><<<total, kDirectThreads, 0, st>>>(b); break;
+    case 3: k_fuse_direct<0, true><<<total, kDirectThreads, 0, st>>>(b); break;
+    case 4: k_fuse_direct<1, true><<<total, kDirectThreads, 0, st>>>(b); break;
+    case 5: k_fuse_direct<2, true><<<total, kDirectThreads, 0, st>>>(b); break;
+    default: k_fuse_direct<0, false><<<total, kDirectThreads, 0, st>>>(b); break;
+  }
   return cudaGetLastError();
 }
 
@@ -153,7 +170,7 @@ cudaError_t launch_fuse_direct(const MapView& mv, const ScanGeom& g, const float
   b.job[0].latest = latest;
   b.job[0].soft = soft;
   b.work = mv.ctr + kCtrWork;
-  return launch_direct_batch(b, soft ? 1 : (latest ? 2 : 0), st);
+  return launch_direct_batch(b, (soft ? 1 : (latest ? 2 : 0)) + (g.weighting ? 3 : 0), st);
 }
 
 }  // namespace slim

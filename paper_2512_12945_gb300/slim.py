@@ -22,6 +22,7 @@ SLIM_CLOSED_ONEHOT, SLIM_CLOSED_SOFT, SLIM_OPEN, SLIM_CLOSED_LATEST = 0, 1, 2, 3
 SLIM_STORE_F32, SLIM_STORE_BF16 = 0, 1
 SLIM_EXTRACT_POSTERIOR = 1
 AGGREGATION = {"auto": 0, "sort": 1, "hash": 2, "direct": 3}
+WEIGHTING = {"constant": 0, "linear": 1}  # slim_weighting
 MODES = {"onehot": SLIM_CLOSED_ONEHOT, "soft": SLIM_CLOSED_SOFT, "open": SLIM_OPEN,
          "latest": SLIM_CLOSED_LATEST}
 STATUS = {0: "SLIM_OK", 1: "SLIM_ERR_ARG", 2: "SLIM_ERR_CUDA", 3: "SLIM_ERR_CAPACITY",
@@ -43,7 +44,8 @@ class slim_map_params(ctypes.Structure):
                 ("alpha0", ctypes.c_double), ("body_from_sensor", ctypes.c_double * 16),
                 ("block_capacity", ctypes.c_int64), ("hash_capacity", ctypes.c_int64),
                 ("voxel_capacity", ctypes.c_int64), ("max_points", ctypes.c_int64),
-                ("aggregation", ctypes.c_int32), ("tile_points", ctypes.c_int32)]
+                ("aggregation", ctypes.c_int32), ("tile_points", ctypes.c_int32),
+                ("weighting", ctypes.c_int32), ("weight_eps", ctypes.c_float)]
 
 
 class slim_stats(ctypes.Structure):
@@ -371,7 +373,7 @@ class Map:
                  embed_storage="f32", min_range=0.0, max_range=1e30, alpha0=1.0,
                  body_from_sensor=None, block_capacity=100000, hash_capacity=262144,
                  voxel_capacity=1000000, max_points=1 << 18, aggregation="auto",
-                 tile_points=0):
+                 tile_points=0, weighting="constant", weight_eps=0.0):
         p = slim_map_params_default()
         p.voxel_size = voxel_size
         p.trunc = trunc
@@ -392,6 +394,8 @@ class Map:
         p.max_points = max_points
         p.aggregation = AGGREGATION[aggregation] if isinstance(aggregation, str) else aggregation
         p.tile_points = tile_points
+        p.weighting = WEIGHTING[weighting] if isinstance(weighting, str) else int(weighting)
+        p.weight_eps = weight_eps
         self.params = p
         self.mode = p.mode
         self.width = embed_dim if p.mode == SLIM_OPEN else num_classes
