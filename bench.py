@@ -37,6 +37,7 @@ METRIC = "points integrated/s (TSDF+Bayes semantic), % HBM roofline, plain vs ch
 UNIT = "points/s"
 COUNTS = os.path.join(ROOT, "tests", "golden", "street_lidar_counts.json")
 INDOOR_COUNTS = os.path.join(ROOT, "tests", "golden", "indoor_rgbd_counts.json")
+ROOM_COUNTS = os.path.join(ROOT, "tests", "golden", "room_lidar_counts.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 K_CLASSES = 20
 
@@ -190,14 +191,14 @@ def open_algorithmic_bytes(n_frames, L, bf16):
                for r in rows[:n_frames])
 
 
-def algorithmic_bytes(counts, n_scans):
+def algorithmic_bytes(counts, n_scans, K=K_CLASSES):
     """B = N_all*12 + N_valid*4K + (2*U_old + U_new)*R + U_b*16 per scan,
     R = 8 + 4K bytes (D, W, K counts)."""
-    R = 8 + 4 * K_CLASSES
+    R = 8 + 4 * K
     out = []
     for row in counts["scans"][:n_scans]:
         old = row["voxels"] - row["new_voxels"]
-        out.append(row["points"] * 12 + row["valid"] * 4 * K_CLASSES +
+        out.append(row["points"] * 12 + row["valid"] * 4 * K +
                    (2 * old + row["new_voxels"]) * R + row["blocks"] * 16)
     return out
 
@@ -697,6 +698,20 @@ def run_indoor(args):
                                                "peak_source": kind},
                                   "hbm_gbs": rows * (2 * 512 + 8) / (kq / 1e3) / 1e9}}
         m.close()
+    # the oracle on the workload's frames (FP64 NIG updates, one observation
+    # at a time; about 2-3 s per frame)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        om = oracle.OracleMap(voxel_size=w.voxel_size, trunc=w.trunc, mode=oracle.OPEN,
+                              embed_dim=512, min_range=w.min_range, max_range=w.max_range,
+                              body_from_sensor=w.body_from_sensor)
+        t = time.perf_counter()
+        nv = sum(om.integrate(s["pts"], s["pose"], s["sem"]) for s in w.scans)
+        dt = time.perf_counter() - t
+        cpu = {"value": nv / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
+               "sample": f"all {len(w.scans)} frames ({nv} valid pixels), {dt:.1f} s "
+                         "single-threaded"}
     # the query kernel at a size where it is a real contraction: 2^20 BF16
     # rows of l = 512 against 256 queries, caller-held rows
     gen = torch.Generator(device="cuda").manual_seed(11)
@@ -721,7 +736,7 @@ def run_indoor(args):
             "dtype": "f32 accumulate, bf16 storage", "data": "synthetic",
             "config": {"workload": f"indoor-rgbd {args.frames} frames 640x480, l=512, voxel "
                                    "0.05 m, trunc 0.15 m, 256 queries T=0.01"},
-            "storage": out, "query_1M_rows": big}
+            "storage": out, "query_1M_rows": big, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -896,11 +911,32 @@ def run_room(args):
     bms = _timed(batched, args.steps, args.warmup, stream)
     m.sync()
     valid = sum(int((np.linalg.norm(s["pts"], axis=1) >= w.min_range).sum()) for s in w.scans)
+    # whole-call roofline of the batched form (all 10 scans in one launch),
+    # algorithmic bytes from the oracle's per-scan counts
+    roof = None
+    try:
+        with open(ROOM_COUNTS) as f:
+            counts = json.load(f)
+        B = sum(algorithmic_bytes(counts, len(w.scans), K=w.num_classes))
+        peak, kind = measured_peak()
+        roof = {"bound": "hbm", "achieved": round(B / (bms / 1e3) / 1e9, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(B / (bms / 1e3) / 1e9 / peak, 4),
+                "peak_source": kind, "algorithmic_bytes_per_step": B,
+                "scope": "slim_map_reset + slim_integrate_batch of the 10 scans"}
+    except (OSError, KeyError, ValueError):
+        pass
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, dt, nv = cpu_oracle_rate(w, len(w.scans))
+        cpu = {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
+               "sample": f"all {len(w.scans)} scans ({nv} valid points), {dt:.2f} s "
+                         "single-threaded"}
     line = {"metric": "points integrated/s (room, 10 scans x 16x512)", "value": valid / (bms / 1e3),
             "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "room 10x10x3 m + 6 objects, 10 scans x 16x512, 10 classes"},
-            "plain_ms_per_step": pms, "batched_ms_per_step": bms}
+            "plain_ms_per_step": pms, "batched_ms_per_step": bms, "roofline": roof,
+            "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0
 
