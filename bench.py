@@ -38,6 +38,7 @@ UNIT = "points/s"
 COUNTS = os.path.join(ROOT, "tests", "golden", "street_lidar_counts.json")
 INDOOR_COUNTS = os.path.join(ROOT, "tests", "golden", "indoor_rgbd_counts.json")
 ROOM_COUNTS = os.path.join(ROOT, "tests", "golden", "room_lidar_counts.json")
+BATCH_COUNTS = os.path.join(ROOT, "tests", "golden", "batch_counts.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 K_CLASSES = 20
 
@@ -823,16 +824,8 @@ def run_batch(args):
     from paper_2512_12945_gb300 import build, slim, synth
     build.build()
     torch.cuda.set_device(0)
-    rng = np.random.default_rng(5)
     n_scans = 10
-    closed, opened = [], []
-    for k in range(8):
-        n_az = int(rng.integers(320, 3900))
-        closed.append(synth.street_lidar(seed=50 + k, n_scans=n_scans, n_az=n_az))
-    sizes = [(320, 240), (400, 300), (480, 360), (640, 480)] * 2
-    for k, (wd, ht) in enumerate(sizes):
-        opened.append(synth.indoor_rgbd(seed=60 + k, n_frames=40, width=wd, height=ht, dim=256,
-                                        frames=list(range(n_scans))))
+    closed, opened = synth.batch_workload(seed=5, n_scans=n_scans)
     maps, items, valid, tiles = [], [], 0, []
     for w in closed:
         m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=20,
@@ -870,6 +863,28 @@ def run_batch(args):
     gms = _timed(graph.replay, args.steps, args.warmup, stream)
     for m in maps:
         m.sync()
+    # whole-step roofline (resets + the batch call, graph replay): algorithmic
+    # bytes of every map's scans from the oracle's per-scan counts; closed
+    # maps R = 8 + 4K, open maps (BF16 m and beta) R = 8 + 4l
+    roof = None
+    try:
+        with open(BATCH_COUNTS) as f:
+            bc = json.load(f)["maps"]
+        B = 0
+        for mp in bc:
+            sin = 4 * mp["width"]
+            R = 8 + 4 * mp["width"]
+            for r in mp["scans"]:
+                B += (r["points"] * 12 + r["valid"] * sin +
+                      (2 * (r["voxels"] - r["new_voxels"]) + r["new_voxels"]) * R +
+                      r["blocks"] * 16)
+        peak, kind = measured_peak()
+        roof = {"bound": "hbm", "achieved": round(B / (gms / 1e3) / 1e9, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(B / (gms / 1e3) / 1e9 / peak, 4),
+                "peak_source": kind, "algorithmic_bytes_per_step": B,
+                "scope": "16 map resets + one slim_integrate_batch (graph replay)"}
+    except (OSError, KeyError, ValueError):
+        pass
     line = {"metric": "batched points integrated/s (16 uneven maps, closed + open)",
             "value": valid / (gms / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f32 / bf16 storage",
@@ -878,7 +893,7 @@ def run_batch(args):
                                    "+ 8 open-set maps (256-dim, 320x240..640x480, bf16), "
                                    f"{n_scans} scans each per step"},
             "graph_ms_per_step": gms, "eager_ms_per_step": ems, "points_per_step": valid,
-            "closed_strategies": tiles}
+            "closed_strategies": tiles, "roofline": roof}
     print(json.dumps(line), flush=True)
     return 0
 

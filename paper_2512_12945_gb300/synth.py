@@ -356,3 +356,19 @@ def random_queries(seed, n, dim):
     """n seeded random unit query vectors (float32)."""
     rng = np.random.default_rng(seed)
     return unit_centroids(rng, n, dim).astype(np.float32)
+
+
+def batch_workload(seed=5, n_scans=10):
+    """The batched multi-map configuration: 8 closed-set street maps (64 beams,
+    azimuth counts drawn from [320, 3900), so 20 k-250 k points per scan) and
+    8 open-set RGB-D maps (l = 256, 320 x 240 to 640 x 480), n_scans scans
+    each. Returns (closed workloads, open workloads)."""
+    rng = np.random.default_rng(seed)
+    closed = []
+    for k in range(8):
+        n_az = int(rng.integers(320, 3900))
+        closed.append(street_lidar(seed=50 + k, n_scans=n_scans, n_az=n_az))
+    sizes = [(320, 240), (400, 300), (480, 360), (640, 480)] * 2
+    opened = [indoor_rgbd(seed=60 + k, n_frames=40, width=wd, height=ht, dim=256,
+                          frames=list(range(n_scans))) for k, (wd, ht) in enumerate(sizes)]
+    return closed, opened
