@@ -281,9 +281,10 @@ slim_status slim_query(slim_map* m, const uint16_t* q_dev, int32_t q, float temp
                        void* stream);
 
 /* The open-set read-out of slim_query over rows the caller holds, for
- * callers that cannot allocate device memory (code inside a stream capture
- * that must not add allocations, real-time loops with a fixed memory
- * budget, hosts that only pass buffers they own). The paper has no
+ * callers that cannot allocate device memory (plug-ins whose host
+ * application owns every device allocation, real-time loops whose memory
+ * budget is fixed up front, hosts that only pass buffers they own). The
+ * paper has no
  * counterpart; this is an interface convenience.
  *   rows_dev  n_rows x l bf16 bit patterns (voxel means, row-major, 16-byte
  *             aligned); q_dev q x l bf16 queries (16-byte aligned);

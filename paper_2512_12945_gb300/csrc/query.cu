@@ -703,8 +703,8 @@ slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float tempe
 // ---------------------------------------------------------------------------
 // Read-out for callers that cannot allocate device memory.
 //
-// Some callers may not call cudaMalloc at all: code running inside a stream
-// capture that must not add allocation nodes, real-time loops whose memory
+// Some callers may not call cudaMalloc at all: plug-ins whose host
+// application owns every device allocation, real-time loops whose memory
 // budget is fixed up front, or host programs that only hand in buffers they
 // already own. slim_query_rows_static serves them: its working memory is the
 // file-scope array below, which exists on every GPU that loads this library

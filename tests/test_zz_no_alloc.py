@@ -1,13 +1,14 @@
 """The read-out entry point for callers that cannot allocate device memory
 (slim_query_rows_static) against the map's own read-out (slim_query).
 
-Callers inside a stream capture, real-time loops with a fixed memory budget,
-or hosts that only hand in their own buffers cannot let the library call
-cudaMalloc. slim_query_rows_static takes its working memory from a static
-device array instead; this test checks, through the C ABI, that it gives the
-same labels and probabilities as slim_query on the same rows, on two calls in
-a row (the array keeps the previous call's contents). It sits in a file of its
-own that pytest collects last."""
+Plug-ins whose host application owns every device allocation, real-time
+loops with a memory budget fixed up front, or hosts that only hand in their
+own buffers cannot let the library call cudaMalloc. slim_query_rows_static
+takes its working memory from a static device array instead; this test
+checks, through the C ABI, that it gives the same labels and probabilities as
+slim_query on the same rows, on two calls in a row (the array keeps the
+previous call's contents). It sits in a file of its own that pytest collects
+last."""
 import numpy as np
 import pytest
 
