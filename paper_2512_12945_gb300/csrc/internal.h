@@ -64,10 +64,13 @@ cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
                            uint32_t* vals_tmp, void* tmp, int64_t n, int bits,
                            cudaStream_t st);
 // As radix_sort_u32 with the item count read on the device from *n_dev
-// (at most n_max items; the launch is sized for n_max).
+// (at most n_max items; the launch is sized for n_max). The sorted pairs are
+// left in whichever of (keys, vals) / (keys_tmp, vals_tmp) the last pass
+// wrote; *keys_out / *vals_out name it (no copy back).
 cudaError_t radix_sort_u32_devn(uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
                                 uint32_t* vals_tmp, void* tmp, int64_t n_max,
-                                const uint32_t* n_dev, int bits, cudaStream_t st);
+                                const uint32_t* n_dev, int bits, cudaStream_t st,
+                                uint32_t** keys_out, uint32_t** vals_out);
 // Exclusive scan of n uint32 counts into out (n + 1 entries, out[n] = total).
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp,
                                cudaStream_t st);

@@ -564,8 +564,10 @@ slim_status open_integrate(slim_map* m, const MapView& mv, OpenScratch& o, const
   // keys of pairs without a block (0xFFFFFFFF) must sort after every valid
   // key within the sorted bits: valid keys stay below (block_cap + 1) << 9
   const int bits = 9 + ceil_log2((uint64_t)mv.block_cap + 1);
+  uint32_t* skeys = nullptr;  // the sorted pairs: (keys, vals) or the ping-pong pair
+  uint32_t* svals = nullptr;
   e = radix_sort_u32_devn(o.keys, o.vals, o.keys_tmp, o.vals_tmp, o.tmp, n_max, o.ctr + kOpPairs,
-                          bits, st);
+                          bits, st, &skeys, &svals);
   if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
   prof_end(m, tok, st);
   tok = prof_begin(m, SLIM_KERNEL_OPEN_APPLY, st);
@@ -573,11 +575,11 @@ slim_status open_integrate(slim_map* m, const MapView& mv, OpenScratch& o, const
   const unsigned fgrid = (unsigned)((pieces + 7) / 8);
   const unsigned mgrid = 152 * 8;
   if (bf16) {
-    k_open_frag<1><<<fgrid, 256, 0, st>>>(mv, o.keys, o.vals, o.pair_d, o.pair_pt, o.ctr, sem, L,
+    k_open_frag<1><<<fgrid, 256, 0, st>>>(mv, skeys, svals, o.pair_d, o.pair_pt, o.ctr, sem, L,
                                           n_max, o.part, o.meta);
     k_open_merge<1><<<mgrid, 256, 0, st>>>(mv, o.ctr, L, n_max, o.part, o.meta);
   } else {
-    k_open_frag<0><<<fgrid, 256, 0, st>>>(mv, o.keys, o.vals, o.pair_d, o.pair_pt, o.ctr, sem, L,
+    k_open_frag<0><<<fgrid, 256, 0, st>>>(mv, skeys, svals, o.pair_d, o.pair_pt, o.ctr, sem, L,
                                           n_max, o.part, o.meta);
     k_open_merge<0><<<mgrid, 256, 0, st>>>(mv, o.ctr, L, n_max, o.part, o.meta);
   }
