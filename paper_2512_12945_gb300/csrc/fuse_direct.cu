@@ -9,11 +9,13 @@
 //
 // Blocks: when a ray enters an 8^3 block, the thread looks the block up in
 // the map's hash (the hash table stays in L2), inserting it if it is new
-// (slot from the allocation counter, published with a release store: the
-// record pool is already zero beyond the counter, see k_zero_used_blocks)
-// or waiting (time-bounded, acquire) for another thread's publication. A
-// publication needs nothing but its own thread's earlier stores, so no wait
-// can be part of a cycle. (A per-CTA shared-memory cache of block slots in
+// (slot from the allocation counter, published with a relaxed store) or
+// waiting (time-bounded) for another thread's publication. The record pool
+// is already zero beyond the counter (see k_zero_used_blocks) and readers
+// use a slot only as the address of their reductions, so a publication
+// orders nothing else and needs no release / acquire pair; the block's key
+// in blk_key is read only by later kernels. A publication needs nothing but
+// its own thread's earlier steps, so no wait can be part of a cycle. (A per-CTA shared-memory cache of block slots in
 // front of the hash was measured slower: 1.81 vs 1.66 ms per 100 scans.)
 //
 // One kernel serves a single scan and a batch of scans of many maps (the
@@ -55,14 +57,14 @@ __device__ __forceinline__ uint32_t map_block_slot(const MapView& mv, uint64_t k
         mv.blk_key[slot] = key;
         v = slot;
       }
-      st_release(&mv.hvals[h], v);
+      st_relaxed(&mv.hvals[h], v);
       return v;
     }
     if (found) {
-      uint32_t v = ld_acquire(&mv.hvals[h]);
+      uint32_t v = ld_relaxed(&mv.hvals[h]);
       if (v == kNoSlot) {
         const uint64_t t0 = global_ns();
-        while ((v = ld_acquire(&mv.hvals[h])) == kNoSlot) {
+        while ((v = ld_relaxed(&mv.hvals[h])) == kNoSlot) {
           if (global_ns() - t0 > kCrossCtaWaitNs) {
             raise_status(mv.ctr, kDevTimeout, 5);
             return kFailSlot;
