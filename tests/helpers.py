@@ -4,7 +4,7 @@ import numpy as np
 
 import oracle
 
-# spec tolerance for FP32 fields (SDF, posteriors)
+# parity tolerance for FP32 fields (SDF, posteriors): relative, absolute
 RTOL, ATOL = 1e-5, 1e-6
 
 
