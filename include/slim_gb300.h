@@ -329,12 +329,17 @@ typedef struct {
   const void* sem_dev;
 } slim_batch_item;
 
-/* Integrate n_items scans, possibly of different maps and sizes, with one
- * launch per phase for all items (work items are scheduled over a shared
- * persistent grid). Items of the same map are fused as one observation set
- * (Theorems 1-2 make the result independent of order and grouping). All
- * maps must live on the current device. Capturable in a CUDA graph when
- * every map was created before capture. */
+/* Integrate n_items scans, possibly of different maps and sizes, in few
+ * launches: closed-set items of maps with direct reductions share one grid
+ * per mode and weighting and per 16 items (one CTA per 256 points of each
+ * item); items of hash-tile maps share one persistent launch per 16 items
+ * (CTAs take tiles of all items from a device counter); open-set and
+ * sort-aggregation items are integrated one by one by their own kernels.
+ * Items of the same map are fused as one observation set (Theorems 1-2 make
+ * the result independent of order and grouping; the latest-label mode keeps
+ * scan order through its stamp). All maps must live on the current device.
+ * Nothing is allocated or read back, so the call is capturable in a CUDA
+ * graph when every map was created before capture. */
 slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items,
                                  void* stream);
 
