@@ -61,8 +61,8 @@ def parse():
     ap.add_argument("--workload", choices=["street", "room", "indoor", "adjoint", "batch", "render"],
                     default="street", help="street (default, the headline line) or a "
                     "secondary configuration, each printing its own JSON line")
-    ap.add_argument("--frames", type=int, default=4, help="indoor: RGB-D frames per step")
-    ap.add_argument("--voxel-capacity", type=int, default=2_000_000,
+    ap.add_argument("--frames", type=int, default=200, help="indoor: RGB-D frames per step")
+    ap.add_argument("--voxel-capacity", type=int, default=400_000,
                     help="indoor: voxel rows reserved per map")
     ap.add_argument("--block-capacity", type=int, default=65536,
                     help="street: 8^3 blocks reserved per map (100 scans use ~26k)")
@@ -625,39 +625,57 @@ def _bf16_peak():
         return 1900.0, "fallback"
 
 
+def _indoor_geometry(f):
+    """Frame f of the indoor RGB-D workload: points (sensor frame), pose and
+    per-pixel object labels (the embeddings are drawn on the device)."""
+    import numpy as np
+    from paper_2512_12945_gb300 import synth
+    w = synth.indoor_rgbd(seed=3, n_frames=200, width=640, height=480, dim=8, frames=[f])
+    s = w.scans[0]
+    return s["pts"], s["pose"], s["labels"].astype(np.int32)
+
+
 def run_indoor(args):
     """Open-set RGB-D frames (640x480, l = 512), FP32 vs BF16 storage, and the
-    tensor-core query of 256 embeddings against every voxel."""
+    tensor-core query of 256 embeddings against every voxel of the map."""
+    import multiprocessing as mp
     import numpy as np
+    nf = args.frames
+    # the frames' geometry on the host cores, before the first GPU call
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        geo = pool.map(_indoor_geometry, range(nf))
     import torch
     from paper_2512_12945_gb300 import build, slim, synth
     build.build()
     torch.cuda.set_device(0)
-    w = synth.indoor_rgbd(seed=3, n_frames=200, width=640, height=480, dim=512,
-                          frames=list(range(args.frames)))
-    pts = [torch.from_numpy(s["pts"]).cuda() for s in w.scans]
-    sem = [torch.from_numpy(s["sem"]).cuda() for s in w.scans]
-    valid = sum(int((np.linalg.norm(s["pts"], axis=1) >= w.min_range).sum()) for s in w.scans)
+    cents = synth.indoor_centroids(3, 512)
+    pts = [torch.from_numpy(g[0]).cuda() for g in geo]
+    sem = [synth.indoor_embeddings_device(torch.from_numpy(g[2]).cuda().long(), cents, 3, f)
+           for f, g in enumerate(geo)]
+    poses = [g[1] for g in geo]
+    valid = sum(int((np.linalg.norm(g[0], axis=1) >= 0.3).sum()) for g in geo)
     fpx = 525.0
-    depths = [torch.from_numpy(np.ascontiguousarray(s["pts"][:, 2].reshape(480, 640),
-                                                    np.float32)).cuda() for s in w.scans]
+    depths = [torch.from_numpy(np.ascontiguousarray(g[0][:, 2].reshape(480, 640),
+                                                    np.float32)).cuda() for g in geo]
+    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+    hbm_peak, hbm_kind = measured_peak()
     out = {}
     for storage in ("f32", "bf16"):
-        m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, mode="open", embed_dim=512,
-                     embed_storage=storage, min_range=w.min_range, max_range=w.max_range,
+        m = slim.Map(voxel_size=0.05, trunc=0.15, mode="open", embed_dim=512,
+                     embed_storage=storage, min_range=0.3, max_range=8.0,
                      max_points=640 * 480, block_capacity=200000, hash_capacity=1 << 20,
-                     voxel_capacity=args.voxel_capacity)
+                     voxel_capacity=args.voxel_capacity, image_width=640)
 
         def step():
             m.reset()
-            for p, q, s in zip(pts, sem, w.scans):
-                m.integrate(p, s["pose"], q)
+            for p, q, pose in zip(pts, sem, poses):
+                m.integrate(p, pose, q)
 
         def step_depth():  # the same frames as z-depth images (RGB-D front end)
             m.reset()
-            for dimg, q, s in zip(depths, sem, w.scans):
-                m.integrate_depth(dimg, fpx, fpx, 320.0, 240.0, s["pose"], q)
+            for dimg, q, pose in zip(depths, sem, poses):
+                m.integrate_depth(dimg, fpx, fpx, 320.0, 240.0, pose, q)
 
         for _ in range(args.warmup):
             step_depth()
@@ -681,38 +699,47 @@ def run_indoor(args):
         kq = qkms / max(nq, 1)
         flops = 2.0 * rows * 512 * 256
         peak, kind = _bf16_peak()
-        B = open_algorithmic_bytes(args.frames, 512, storage == "bf16")
-        hbm_peak, hbm_kind = measured_peak()
+        B = open_algorithmic_bytes(nf, 512, storage == "bf16")
+        kern = {k: v[1] / args.steps for k, v in prof.items()}
+        integ = kern.get("open_tile", 0.0) + kern.get("open_apply", 0.0)
         roof = None if B is None else {
             "bound": "hbm", "achieved": round(B / (ms / 1e3) / 1e9, 1), "peak": hbm_peak,
             "unit": "GB/s", "frac": round(B / (ms / 1e3) / 1e9 / hbm_peak, 4),
             "peak_source": hbm_kind, "algorithmic_bytes_per_step": B,
-            "scope": "whole integration call per frame (traverse, pairs, sort, fragments, merge)"}
-        out[storage] = {"points_per_s": valid * args.steps / (ms * args.steps / 1e3),
-                        "ms_per_step": ms, "voxels": rows, "integrate_roofline": roof,
+            "kernels_frac": round(B / (integ / 1e3) / 1e9 / hbm_peak, 4) if integ else None,
+            "scope": "a step: map reset + one slim_integrate per frame (k_open_tile, "
+                     "k_open_apply); kernels_frac: the same bytes over the two kernels' "
+                     "event time alone"}
+        out[storage] = {"points_per_s": valid / (ms / 1e3), "ms_per_step": ms,
+                        "ms_per_frame": ms / nf, "voxels": rows, "integrate_roofline": roof,
                         "depth_front_end": {"ms_per_step": dms,
                                             "points_per_s": valid / (dms / 1e3),
                                             "call": "slim_integrate_depth per frame"},
-                        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
-                        "query": {"ms": qms, "kernel_ms": kq, "tflops": flops / (kq / 1e3) / 1e12,
+                        "kernels_ms_per_step": kern,
+                        "query": {"rows": rows, "ms": qms, "kernel_ms": kq,
+                                  "tflops": flops / (kq / 1e3) / 1e12,
                                   "roofline": {"bound": "tensor", "peak": peak, "unit": "TFLOP/s",
                                                "frac": flops / (kq / 1e3) / 1e12 / peak,
                                                "peak_source": kind},
                                   "hbm_gbs": rows * (2 * 512 + 8) / (kq / 1e3) / 1e9}}
         m.close()
-    # the oracle on the workload's frames (FP64 NIG updates, one observation
-    # at a time; about 2-3 s per frame)
+    del sem
+    torch.cuda.empty_cache()
+    # the oracle as it stands on the first frames (FP64 NIG updates, one
+    # observation at a time; numpy-drawn embeddings of the same distribution)
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
-        om = oracle.OracleMap(voxel_size=w.voxel_size, trunc=w.trunc, mode=oracle.OPEN,
-                              embed_dim=512, min_range=w.min_range, max_range=w.max_range,
-                              body_from_sensor=w.body_from_sensor)
+        wc = synth.indoor_rgbd(seed=3, n_frames=200, width=640, height=480, dim=512,
+                               frames=[0, 1])
+        om = oracle.OracleMap(voxel_size=wc.voxel_size, trunc=wc.trunc, mode=oracle.OPEN,
+                              embed_dim=512, min_range=wc.min_range, max_range=wc.max_range,
+                              body_from_sensor=wc.body_from_sensor)
         t = time.perf_counter()
-        nv = sum(om.integrate(s["pts"], s["pose"], s["sem"]) for s in w.scans)
+        nv = sum(om.integrate(s["pts"], s["pose"], s["sem"]) for s in wc.scans)
         dt = time.perf_counter() - t
         cpu = {"value": nv / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
-               "sample": f"all {len(w.scans)} frames ({nv} valid pixels), {dt:.1f} s "
+               "sample": f"first {len(wc.scans)} frames ({nv} valid pixels), {dt:.1f} s "
                          "single-threaded"}
     # the query kernel at a size where it is a real contraction: 2^20 BF16
     # rows of l = 512 against 256 queries, caller-held rows
@@ -730,14 +757,18 @@ def run_indoor(args):
            "tflops": flops / (sms / 1e3) / 1e12,
            "tensor_frac": flops / (sms / 1e3) / 1e12 / peak, "tensor_peak": peak,
            "hbm_gbs": nrow * 512 * 2 / (sms / 1e3) / 1e9,
-           "hbm_frac": nrow * 512 * 2 / (sms / 1e3) / 1e9 / measured_peak()[0],
-           "peak_source": kind, "call": "slim_query_rows_static (row norms + tcgen05 GEMM + epilogue)"}
+           "hbm_frac": nrow * 512 * 2 / (sms / 1e3) / 1e9 / hbm_peak,
+           "peak_source": kind,
+           "call": "slim_query_rows_static (row norms + tcgen05 GEMM + epilogue; waits for "
+                   "its stream)"}
     line = {"metric": "open-set points integrated/s (NIG, l=512) and query TFLOP/s",
             "value": out["bf16"]["points_per_s"], "unit": "points/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "dtype": "f32 accumulate, bf16 storage", "data": "synthetic",
-            "config": {"workload": f"indoor-rgbd {args.frames} frames 640x480, l=512, voxel "
-                                   "0.05 m, trunc 0.15 m, 256 queries T=0.01"},
+            "config": {"workload": f"indoor-rgbd {nf} frames 640x480, l=512, voxel 0.05 m, "
+                                   "trunc 0.15 m, 256 queries T=0.01",
+                       "inputs": "all frames resident in HBM (126 GB of embeddings at 200 "
+                                 "frames), larger than L2"},
             "storage": out, "query_1M_rows": big, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0
@@ -847,11 +878,15 @@ def run_batch(args):
         tiles.append(m.autotune(torch.from_numpy(s0["pts"]).cuda(), s0["pose"],
                                 torch.from_numpy(s0["sem"]).cuda()))
         maps.append(m)
+    open_tiles = []
     for w in opened:
         m = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, mode="open", embed_dim=256,
                      embed_storage="bf16", min_range=w.min_range, max_range=w.max_range,
-                     max_points=w.scans[0]["pts"].shape[0], voxel_capacity=1500000,
-                     block_capacity=60000, hash_capacity=1 << 18)
+                     max_points=w.scans[0]["pts"].shape[0], voxel_capacity=300000,
+                     block_capacity=60000, hash_capacity=1 << 18, image_width=w.image_width)
+        s0 = w.scans[0]
+        open_tiles.append(m.autotune(torch.from_numpy(s0["pts"]).cuda(), s0["pose"],
+                                     torch.from_numpy(s0["sem"]).cuda()))
         maps.append(m)
     for m, w in zip(maps, closed + opened):
         for s in w.scans:
@@ -872,6 +907,15 @@ def run_batch(args):
         eager()
     ems = _timed(eager, args.steps, args.warmup, stream)
     gms = _timed(graph.replay, args.steps, args.warmup, stream)
+    # kernel time per step by kind (eager run, events on the launch stream)
+    for m in maps:
+        slim.slim_profile_enable(m.handle, True)
+    eager()
+    kern = {}
+    for m in maps:
+        for k, v in slim.slim_profile_read(m.handle).items():
+            kern[k] = kern.get(k, 0.0) + v[1]
+        slim.slim_profile_enable(m.handle, False)
     for m in maps:
         m.sync()
     # whole-step roofline (resets + the batch call, graph replay): algorithmic
@@ -904,7 +948,11 @@ def run_batch(args):
                                    "+ 8 open-set maps (256-dim, 320x240..640x480, bf16), "
                                    f"{n_scans} scans each per step"},
             "graph_ms_per_step": gms, "eager_ms_per_step": ems, "points_per_step": valid,
-            "closed_strategies": tiles, "roofline": roof}
+            "autotuner": {"closed": {"choices": tiles,
+                                     "meaning": "0 = direct reductions, else hash-tile points"},
+                          "open": {"choices": open_tiles,
+                                   "meaning": "tile width in pixels (tiles of 256 pixels)"}},
+            "kernels_ms_per_step": kern, "roofline": roof}
     print(json.dumps(line), flush=True)
     return 0
 

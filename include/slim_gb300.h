@@ -123,9 +123,17 @@ typedef struct {
   int64_t max_points;      /* largest scan passed to slim_integrate */
   int32_t aggregation;     /* slim_aggregation: how pairs reach the records */
   int32_t tile_points;     /* hash aggregation: points per CTA tile, 64, 128 or
-                              256 (0 = 256); see slim_autotune */
+                              256 (0 = 256); SLIM_OPEN with image_width > 0:
+                              tile width in pixels, 8, 16 or 32 (0 = 16; tiles
+                              hold 256 pixels); see slim_autotune */
   int32_t weighting;       /* slim_weighting (default SLIM_WEIGHT_CONSTANT) */
   float weight_eps;        /* SLIM_WEIGHT_LINEAR: metres, 0 <= eps < trunc */
+  int32_t image_width;     /* SLIM_OPEN: the points of a scan are the pixels of a
+                              row-major image of this many columns (an RGB-D
+                              frame back-projected), so integration groups them
+                              in 16 x 16 pixel tiles; 0 (default): unorganized,
+                              tiles of 256 consecutive points. Results do not
+                              depend on it. 0 .. 65536 */
 } slim_map_params;
 
 typedef struct slim_map slim_map;
@@ -284,22 +292,25 @@ slim_status slim_query(slim_map* m, const uint16_t* q_dev, int32_t q, float temp
  * callers that cannot allocate device memory (plug-ins whose host
  * application owns every device allocation, real-time loops whose memory
  * budget is fixed up front, hosts that only pass buffers they own). The
- * paper has no
- * counterpart; this is an interface convenience.
+ * paper has no counterpart; this is an interface convenience.
  *   rows_dev  n_rows x l bf16 bit patterns (voxel means, row-major, 16-byte
  *             aligned); q_dev q x l bf16 queries (16-byte aligned);
  *   label_dev, prob_dev  n_rows outputs as in slim_query.
  * It calls no cudaMalloc / cudaFree and no allocating library routine: its
- * working memory (query norms, a status word) is one static array in device
- * memory, present on every GPU that loads the library until the process
- * exits; the row norms are computed inside the query kernel from the tiles
- * it already loads. At most 2^20 rows and 256 queries per call; larger
- * requests return SLIM_ERR_ARG. The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress, with the device
- * current) and opts the query kernel into its shared memory; make that first
- * call before any stream capture. Every call shares the array and leaves its
- * contents behind; calls whose work overlaps on the GPU (other streams, other
- * threads) race on it, so serialise them. Asynchronous on `stream`. */
+ * working memory (the inverse norms of up to 256 queries and a few status
+ * words, about 1 KB) is one static array in device memory, present on every
+ * GPU that loads the library until the process exits; the row norms are
+ * computed inside the query kernel from the tiles it already loads. At most
+ * 2^20 rows and 256 queries per call; larger requests return SLIM_ERR_ARG.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current) and opts the query kernel
+ * into its shared memory; make that first call before any stream capture.
+ * Every call shares the array and leaves its contents behind (the status
+ * words are cleared at the start of each call); calls whose work overlaps on
+ * the GPU (other streams, other threads) race on it, so serialise them.
+ * The call queues its work on `stream`, then waits for it and returns
+ * SLIM_ERR_TIMEOUT if a bounded wait inside the query kernel ran out (the
+ * outputs are then incomplete). */
 slim_status slim_query_rows_static(const uint16_t* rows_dev, int64_t n_rows, int32_t l,
                                    const uint16_t* q_dev, int32_t q, float temperature, float tp,
                                    int32_t* label_dev, float* prob_dev, void* stream);
@@ -333,7 +344,9 @@ typedef struct {
  * launches: closed-set items of maps with direct reductions share one grid
  * per mode and weighting and per 16 items (one CTA per 256 points of each
  * item); items of hash-tile maps share one persistent launch per 16 items
- * (CTAs take tiles of all items from a device counter); open-set and
+ * (CTAs take tiles of all items from a device counter); open-set items
+ * share one tile grid per embedding storage and 16 items (one CTA per pixel
+ * tile of each item) and one update launch per storage and 16 maps;
  * sort-aggregation items are integrated one by one by their own kernels.
  * Items of the same map are fused as one observation set (Theorems 1-2 make
  * the result independent of order and grouping; the latest-label mode keeps
@@ -343,14 +356,19 @@ typedef struct {
 slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items,
                                  void* stream);
 
-/* Strategy autotuner (no counterpart in the paper). For a closed-set one-hot
- * map (aggregation AUTO, HASH or DIRECT), integrates 8 copies of the given
- * scan (same arguments as slim_integrate) per launch with every candidate:
- * direct reductions (AUTO, DIRECT) and hash tiles of 64, 128 and 256 points
- * (AUTO, HASH); times each with CUDA events on `stream`, keeps the fastest
- * for this map and writes it to *best_tile (0 = direct; may be NULL). The
- * map is reset (emptied) before each trial and at the end. Synchronous.
- * Soft-count, sort-aggregation and open-set maps return
+/* Strategy autotuner (no counterpart in the paper). Times candidates on the
+ * caller's scan (same arguments as slim_integrate) with CUDA events on
+ * `stream`, keeps the fastest for this map and writes it to *best_tile (may
+ * be NULL). The map is reset (emptied) before each trial and at the end.
+ * Synchronous.
+ *   closed-set one-hot maps (aggregation AUTO, HASH or DIRECT): 8 copies of
+ *     the scan per launch with direct reductions (AUTO, DIRECT) and hash
+ *     tiles of 64, 128 and 256 points (AUTO, HASH); *best_tile = 0 for
+ *     direct, else the tile's points;
+ *   open-set maps of organized frames (image_width > 0): tiles of 8 x 32,
+ *     16 x 16 and 32 x 8 pixels; *best_tile = the tile width in pixels
+ *     (unorganized open-set maps have one tiling: *best_tile = 0).
+ * Soft-count, latest-label and sort-aggregation maps return
  * SLIM_ERR_UNSUPPORTED. */
 slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
                           const double pose_host[16], const void* sem_dev, void* stream,
@@ -360,8 +378,8 @@ slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
 typedef enum {
   SLIM_KERNEL_TRAVERSE = 0,     /* band DDA + block allocation */
   SLIM_KERNEL_FUSE_CLOSED = 1,  /* closed-set tile sort + segmented reduce */
-  SLIM_KERNEL_OPEN_PAIRS = 2,   /* open-set pair generation + voxel sort */
-  SLIM_KERNEL_OPEN_APPLY = 3,   /* open-set segmented NIG apply */
+  SLIM_KERNEL_OPEN_TILE = 2,    /* open-set band DDA + on-chip aggregation per tile */
+  SLIM_KERNEL_OPEN_APPLY = 3,   /* open-set NIG update of the touched voxels */
   SLIM_KERNEL_QUERY = 4,        /* tensor-core query GEMM + epilogue */
   SLIM_KERNEL_BACKWARD = 5,     /* adjoint gather */
   SLIM_KERNEL_BATCH = 6,        /* batched persistent integration */

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) k_backward(MapView mv, ScanGeom g,
         Wv = mv.tsdf[row].y;
         gi = (size_t)row;
       } else {
-        Wv = rec_weight(mv.rec + vox * mv.rs, mv.K, mv.split);
+        Wv = rec_weight(mv.rec + vox * mv.rs, mv.K, mv.layout);
         gi = vox;
       }
       const float invW = 1.0f / Wv;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) k_backward_closed(MapView mv, ScanGeom g,
       }
       if (slot >= mv.block_cap) return;
       const size_t vox = (size_t)slot * kBlockVoxels + local_index(i0, i1, i2);
-      const float Wv = rec_weight(mv.rec + vox * mv.rs, mv.K, mv.split);
+      const float Wv = rec_weight(mv.rec + vox * mv.rs, mv.K, mv.layout);
       const float invW = 1.0f / Wv;
       if (sem_grad)
         for (int k = 0; k < K; ++k) out[k] += gS[vox * (size_t)K + k];

@@ -146,9 +146,14 @@ slim_status check_params(const slim_map_params* p) {
     return fail(SLIM_ERR_ARG, "hash_capacity must be in [32, 2^32]");
   if (p->max_points < 0 || p->max_points > ((int64_t)1 << 31))
     return fail(SLIM_ERR_ARG, "max_points must be in [0, 2^31]");
-  if (p->tile_points != 0 && p->tile_points != 64 && p->tile_points != 128 &&
-      p->tile_points != 256)
+  if (p->mode == SLIM_OPEN) {
+    if (p->tile_points != 0 && p->tile_points != 8 && p->tile_points != 16 &&
+        p->tile_points != 32)
+      return fail(SLIM_ERR_ARG, "open set: tile_points (tile width) must be 0, 8, 16 or 32");
+  } else if (p->tile_points != 0 && p->tile_points != 64 && p->tile_points != 128 &&
+             p->tile_points != 256) {
     return fail(SLIM_ERR_ARG, "tile_points must be 0 (default), 64, 128 or 256");
+  }
   if (p->aggregation < 0 || p->aggregation > 3)
     return fail(SLIM_ERR_ARG, "aggregation must be 0 (auto), 1 (sort), 2 (hash) or 3 (direct)");
   if (p->aggregation == SLIM_AGG_HASH && p->mode != SLIM_CLOSED_ONEHOT)
@@ -168,6 +173,8 @@ slim_status check_params(const slim_map_params* p) {
     if (!(p->weight_eps >= 0.f) || !(p->weight_eps < p->trunc))
       return fail(SLIM_ERR_ARG, "weight_eps must be in [0, trunc)");
   }
+  if (p->image_width < 0 || p->image_width > 65536)
+    return fail(SLIM_ERR_ARG, "image_width must be in [0, 65536]");
   return SLIM_OK;
 }
 
@@ -209,12 +216,11 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   m->K = p->mode == SLIM_OPEN ? 0 : p->num_classes;
   m->L = p->mode == SLIM_OPEN ? p->embed_dim : 0;
   m->bf16 = (p->mode == SLIM_OPEN && p->embed_storage == SLIM_STORE_BF16) ? 1 : 0;
-  // one-hot records keep (S_k, c_k) per class, soft records (S, W, c_k)
-  // record floats: one-hot {S_k, c_k} per class; soft {S, W, pad, pad, c_k}
-  // (counts 16-byte aligned for vector reductions); latest {S, W, stamp}
+  // record floats: one-hot {S_k, c_k} per class (FP32); soft {S, W, c_k}
+  // as 64-bit fixed point (exact sums); latest {S, W, stamp}
   m->rs = p->mode == SLIM_CLOSED_ONEHOT  ? (2 * m->K + 3) / 4 * 4
           : p->mode == SLIM_CLOSED_LATEST ? 4
-                                          : ((kSoftCnt + m->K) + 3) / 4 * 4;
+                                          : 2 * (2 + m->K);
   const double q = 2.0 * (double)p->trunc / (double)p->voxel_size;
   m->cap = 3 * (int)std::ceil(q) + 3;
   const int span = (int)std::ceil(q) + 2;
@@ -252,7 +258,9 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   mv.block_cap = (uint32_t)bc;
   mv.rs = m->rs;
   mv.K = m->K;
-  mv.split = p->mode == SLIM_CLOSED_ONEHOT ? 1 : 0;
+  mv.layout = p->mode == SLIM_CLOSED_ONEHOT ? kRecSplit
+              : p->mode == SLIM_CLOSED_SOFT ? kRecSoftFx
+                                            : kRecLatest;
   if (m->mode != SLIM_OPEN) {
     if ((s = m->alloc(&mv.rec, bc * kBlockVoxels * (uint64_t)m->rs)) != SLIM_OK) return bail(s);
     // the pool stays zero beyond the allocation counter (reset re-zeroes
@@ -265,6 +273,9 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
     unsigned char* mr = nullptr;
     unsigned char* br = nullptr;
     if ((s = m->alloc(&mv.vox_row, bc * kBlockVoxels)) != SLIM_OK) return bail(s);
+    // every voxel-row table starts empty (-1); reset restores the used ones
+    if (cudaMemset(mv.vox_row, 0xFF, bc * kBlockVoxels * sizeof(int32_t)) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "cudaMemset"));
     if ((s = m->alloc(&mv.tsdf, rc)) != SLIM_OK) return bail(s);
     if ((s = m->alloc(&mr, rc * m->L * esz)) != SLIM_OK) return bail(s);
     if ((s = m->alloc(&br, rc * m->L * esz)) != SLIM_OK) return bail(s);
@@ -279,7 +290,8 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
       m->qscratch.abf = abf;
       if ((s = m->alloc(&m->qscratch.rnorm2, rc)) != SLIM_OK) return bail(s);
     }
-    if ((s = open_alloc_scratch(m, m->open, p->max_points)) != SLIM_OK) return bail(s);
+    if ((s = open_alloc_scratch(m, m->open)) != SLIM_OK) return bail(s);
+    m->open.tw_log2 = p->tile_points == 8 ? 3 : (p->tile_points == 32 ? 5 : 4);
   }
   const int64_t mp = std::max<int64_t>(p->max_points, 1);
   if ((s = m->alloc(&m->stage_pts, (size_t)mp * 3)) != SLIM_OK) return bail(s);
@@ -304,7 +316,7 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   cudaError_t e = cudaSuccess;
   if (m->mode != SLIM_OPEN) e = closed_setup_attributes(m->mode, m->K, m->tile_points);
   else {
-    e = open_setup_attributes(m);
+    e = open_setup_attributes();
     if (e == cudaSuccess) e = query_setup_attributes();
   }
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaFuncSetAttribute"));
@@ -336,11 +348,12 @@ slim_status slim_map_reset(slim_map* m, void* stream) {
   if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nh = (size_t)m->n_entries;
-  if (m->mode != SLIM_OPEN) {
-    const int tok = prof_begin(m, SLIM_KERNEL_RESET, st);
+  const int tok = prof_begin(m, SLIM_KERNEL_RESET, st);
+  if (m->mode != SLIM_OPEN)
     SLIM_CUDA(launch_zero_used_blocks(m->mv, st));
-    prof_end(m, tok, st);
-  }
+  else
+    SLIM_CUDA(launch_reset_vox_rows(m->mv, st));
+  prof_end(m, tok, st);
   SLIM_CUDA(cudaMemsetAsync(m->mv.hkeys, 0xFF, nh * sizeof(uint64_t), st));
   SLIM_CUDA(cudaMemsetAsync(m->mv.hvals, 0xFF, nh * sizeof(uint32_t), st));
   SLIM_CUDA(cudaMemsetAsync(m->mv.ctr, 0, kNumCounters * sizeof(uint32_t), st));
@@ -381,10 +394,7 @@ slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
     prof_end(m, tok, st);
     return SLIM_OK;
   }
-  const int tok = prof_begin(m, SLIM_KERNEL_TRAVERSE, st);
-  SLIM_CUDA(launch_traverse_alloc(m->mv, g, pts_dev, n, true, st));
-  prof_end(m, tok, st);
-  return open_integrate(m, m->mv, m->open, g, pts_dev, sem, n, m->L, m->bf16, st);
+  return open_integrate(m, g, pts_dev, sem, n, m->p.image_width, st);
 }
 
 slim_status slim_integrate_depth(slim_map* m, const float* depth_dev, int32_t width,
@@ -430,10 +440,7 @@ slim_status slim_integrate_depth(slim_map* m, const float* depth_dev, int32_t wi
     prof_end(m, tok, st);
     return SLIM_OK;
   }
-  const int tok = prof_begin(m, SLIM_KERNEL_TRAVERSE, st);
-  SLIM_CUDA(launch_traverse_alloc(m->mv, g, nullptr, n, true, st));
-  prof_end(m, tok, st);
-  return open_integrate(m, m->mv, m->open, g, nullptr, sem, n, m->L, m->bf16, st);
+  return open_integrate(m, g, nullptr, sem, n, width, st);
 }
 
 slim_status slim_integrate_host(slim_map* m, const float* pts_host, int64_t n,
@@ -452,10 +459,76 @@ slim_status slim_integrate_host(slim_map* m, const float* pts_host, int64_t n,
   return slim_integrate(m, m->stage_pts, n, pose_host, m->stage_sem, stream);
 }
 
+// Open-set maps of organized frames: time the tile shapes 8 x 32, 16 x 16
+// and 32 x 8 pixels on the caller's scan (3 integration calls each after 2
+// untimed ones, CUDA events) and keep the fastest.
+static slim_status open_autotune(slim_map* m, const float* pts_dev, int64_t n,
+                                 const double pose_host[16], const void* sem_dev,
+                                 cudaStream_t st, int32_t* best_tile) {
+  if (m->p.image_width <= 0) {  // unorganized points: one tiling only
+    if (best_tile) *best_tile = 0;
+    return SLIM_OK;
+  }
+  ScanGeom g;
+  compose_pose(pose_host, m->p.body_from_sensor, g, m->p.voxel_size, m->p.trunc,
+               m->p.min_range, m->p.max_range, m->cap, m->p.weighting, m->p.weight_eps);
+  g.scan_no = 1;
+  const bool prof = m->prof_on;
+  m->prof_on = false;
+  const int saved = m->open.tw_log2;
+  cudaEvent_t e0, e1;
+  SLIM_CUDA(cudaEventCreate(&e0));
+  SLIM_CUDA(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int best = saved;
+  slim_status s = SLIM_OK;
+  for (int tw = 3; tw <= 5 && s == SLIM_OK; ++tw) {
+    m->open.tw_log2 = tw;
+    if ((s = slim_map_reset(m, st)) != SLIM_OK) break;
+    for (int r = 0; r < 5 && s == SLIM_OK; ++r) {
+      if (r == 2 && cudaEventRecord(e0, st) != cudaSuccess) s = cuda_fail(cudaGetLastError(), "event");
+      if (s == SLIM_OK)
+        s = open_integrate(m, g, pts_dev, static_cast<const float*>(sem_dev), n,
+                           m->p.image_width, st);
+    }
+    if (s != SLIM_OK) break;
+    cudaError_t e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "autotune");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = tw;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->prof_on = prof;
+  m->open.tw_log2 = s == SLIM_OK ? best : saved;
+  const slim_status r = slim_map_reset(m, st);
+  if (s != SLIM_OK) return s;
+  if (r != SLIM_OK) return r;
+  SLIM_CUDA(cudaStreamSynchronize(st));
+  if (best_tile) *best_tile = 1 << m->open.tw_log2;
+  return SLIM_OK;
+}
+
 slim_status slim_autotune(slim_map* m, const float* pts_dev, int64_t n,
                           const double pose_host[16], const void* sem_dev, void* stream,
                           int32_t* best_tile) {
   if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
+  if (m->mode == SLIM_OPEN) {
+    if (n < 1 || n > m->p.max_points) return fail(SLIM_ERR_ARG, "n must be in [1, max_points]");
+    if (!pts_dev || !sem_dev || !pose_host || !finite_pose(pose_host))
+      return fail(SLIM_ERR_ARG, "pts, sem or pose missing");
+    if (reinterpret_cast<uintptr_t>(sem_dev) & 15)
+      return fail(SLIM_ERR_ARG, "open-set embeddings must be 16-byte aligned");
+    return open_autotune(m, pts_dev, n, pose_host, sem_dev, (cudaStream_t)stream, best_tile);
+  }
   if (m->mode != SLIM_CLOSED_ONEHOT || m->p.aggregation == SLIM_AGG_SORT)
     return fail(SLIM_ERR_UNSUPPORTED, "autotune serves closed one-hot maps (hash or direct)");
   if (n < 1 || n > m->p.max_points) return fail(SLIM_ERR_ARG, "n must be in [1, max_points]");
@@ -768,6 +841,7 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
     nb[q].n_jobs = 0;
     return e == cudaSuccess ? SLIM_OK : cuda_fail(e, "launch_direct_batch");
   };
+  std::vector<OpenItem> open_items;
   for (int32_t k = 0; k < n_items; ++k) {
     const slim_batch_item& it = items[k];
     slim_map* m = it.map;
@@ -816,6 +890,17 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
         slim_status s = flush();
         if (s != SLIM_OK) return s;
       }
+    } else if (m->mode == SLIM_OPEN) {
+      OpenItem oi;
+      oi.map = m;
+      compose_pose(it.pose, m->p.body_from_sensor, oi.g, m->p.voxel_size, m->p.trunc,
+                   m->p.min_range, m->p.max_range, m->cap, m->p.weighting, m->p.weight_eps);
+      oi.g.scan_no = (uint32_t)m->scans;
+      oi.pts = it.pts_dev;
+      oi.sem = static_cast<const float*>(it.sem_dev);
+      oi.n = it.n;
+      oi.width = m->p.image_width;
+      open_items.push_back(oi);
     } else {
       m->scans--;  // counted again by slim_integrate
       slim_status s = slim_integrate(m, it.pts_dev, it.n, it.pose, it.sem_dev, stream);
@@ -826,7 +911,9 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
     slim_status s = flush_direct(q);
     if (s != SLIM_OK) return s;
   }
-  return flush();
+  slim_status s = flush();
+  if (s != SLIM_OK) return s;
+  return open_integrate_batch(open_items, st);
 }
 
 }  // extern "C"

@@ -13,29 +13,6 @@ __device__ __forceinline__ uint32_t tile_hash(uint64_t kb) {
   return h ^ (h >> 15);
 }
 
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Relaxed (non-caching, coherent at gpu scope) 32-bit load and store: for a
-// slot published to readers that only use it as an address into records
-// the pool already holds zeroed, so no ordering with other data is needed.
-__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // Index of the largest of K probabilities (ties to the lowest index). The
 // loads of a group of 16 are issued together before any comparison.
 __device__ __forceinline__ uint32_t argmax_row(const float* __restrict__ row, int K) {

@@ -9,7 +9,17 @@ constexpr uint64_t kEmptyKey = ~0ull;     // empty hash entry
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu; // hash entry without a block slot (yet)
 constexpr uint32_t kFailSlot = 0xFFFFFFFEu; // block could not get a slot (capacity)
 constexpr int kBlockVoxels = 512;         // 8^3 voxels per block
-constexpr int kSoftCnt = 4;  // soft-count records {S, W, pad, pad, c_0..}: counts 16-byte aligned
+// Closed-set record layouts (MapView::layout).
+enum RecLayout : int32_t {
+  kRecLatest = 0,  // latest label: {S, W, stamp (u64)} in FP32 / u64
+  kRecSplit = 1,   // one-hot: {S_0, c_0, ..., S_{K-1}, c_{K-1}} in FP32
+  kRecSoftFx = 2   // soft counts: {S, W, c_0 .. c_{K-1}} as 64-bit fixed point
+};
+// Fixed-point unit of soft-count records: 2^-32 (metres for S, observations
+// for W and the class counts). Scaling a float by 2^32 is exact, so a value
+// of magnitude >= 2^-8 converts without rounding; smaller ones round to
+// 2^-33 at most. Integer sums are exact and independent of their order.
+constexpr float kFxScale = 4294967296.0f;
 
 // Device counters held by each map.
 enum Counter : int {
@@ -43,15 +53,16 @@ struct MapView {
   uint64_t* blk_key;    // [block_cap] key of each allocated slot
   uint32_t block_cap;
   uint32_t* ctr;        // kNumCounters counters
-  // closed set: AoS records of rs floats per voxel.
-  //   one-hot (split = 1): {S_0, c_0, S_1, c_1, ..., S_{K-1}, c_{K-1}, pad}
+  // closed set: AoS records of rs floats per voxel (layout: RecLayout).
+  //   one-hot (kRecSplit): {S_0, c_0, S_1, c_1, ..., S_{K-1}, c_{K-1}, pad}
   //     with c_k the count of class k and S_k the sum of the SDF of those
   //     observations; W = sum c_k and S = W D = sum S_k at read-out.
-  //   soft (split = 0):    {S = W D, W, c_0 .. c_{K-1}, pad}
+  //   soft (kRecSoftFx): int64 {S, W, c_0 .. c_{K-1}} in units of 2^-32
+  //   latest (kRecLatest): {S, W, stamp}
   float* rec;
   int32_t rs;
   int32_t K;
-  int32_t split;
+  int32_t layout;
   // open set
   int32_t* vox_row;     // [block_cap * 512] voxel row or -1
   float2* tsdf;         // [row_cap] (S = W*D, W)
@@ -119,12 +130,35 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Relaxed (non-caching, coherent at gpu scope) 32-bit load and store: for a
+// slot published to readers that only use it as an address into records
+// the pool already holds zeroed, so no ordering with other data is needed.
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+
 // addr[0] += a, addr[1] += b as one vector reduction (addr 8-byte aligned).
 __device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
 }
 
-// Weight W of a closed-set voxel record.
 // r[0..3] += (a, b, c, d) without a return value (16-byte aligned).
 __device__ __forceinline__ void red_add_v4(float* r, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(r), "f"(a), "f"(b), "f"(c),
@@ -132,11 +166,69 @@ __device__ __forceinline__ void red_add_v4(float* r, float a, float b, float c, 
                : "memory");
 }
 
-__device__ __forceinline__ float rec_weight(const float* r, int K, int split) {
-  if (!split) return r[1];
-  float w = 0.f;
-  for (int k = 0; k < K; ++k) w += r[2 * k + 1];
-  return w;
+// *a += v (64-bit integer reduction, no return value; a 8-byte aligned).
+__device__ __forceinline__ void red_add_u64(unsigned long long* a, unsigned long long v) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+
+// x in fixed point of unit 2^-32 (two's complement bits).
+__device__ __forceinline__ unsigned long long fx32(float x) {
+  return (unsigned long long)__float2ll_rn(__fmul_rn(x, kFxScale));
+}
+__device__ __forceinline__ float unfx32(long long q) {
+  return __fmul_rn(__ll2float_rn(q), 1.0f / kFxScale);
+}
+__device__ __forceinline__ const long long* rec_fx(const float* r) {
+  return reinterpret_cast<const long long*>(r);
+}
+
+// (S, W) of a closed-set voxel record (S = W D).
+__device__ __forceinline__ float2 rec_sw(const float* r, int K, int layout) {
+  if (layout == kRecSoftFx) {
+    const long long* q = rec_fx(r);
+    return make_float2(unfx32(q[0]), unfx32(q[1]));
+  }
+  if (layout == kRecLatest) return make_float2(r[0], r[1]);
+  float s = 0.f, w = 0.f;
+  for (int k = 0; k < K; ++k) {
+    s += r[2 * k];
+    w += r[2 * k + 1];
+  }
+  return make_float2(s, w);
+}
+
+// D = S / W of a closed-set record (0 where W = 0); soft records divide the
+// exact fixed-point sums.
+__device__ __forceinline__ float rec_sdf(const float* r, int K, int layout) {
+  if (layout == kRecSoftFx) {
+    const long long* q = rec_fx(r);
+    return q[1] > 0 ? __ll2float_rn(q[0]) / __ll2float_rn(q[1]) : 0.f;
+  }
+  const float2 sw = rec_sw(r, K, layout);
+  return sw.y > 0.f ? sw.x / sw.y : 0.f;
+}
+
+// Weight W of a closed-set voxel record.
+__device__ __forceinline__ float rec_weight(const float* r, int K, int layout) {
+  return rec_sw(r, K, layout).y;
+}
+
+// Count of class k (one-hot and soft records).
+__device__ __forceinline__ float rec_count(const float* r, int k, int layout) {
+  if (layout == kRecSoftFx) return unfx32(rec_fx(r)[2 + k]);
+  return r[2 * k + 1];
+}
+
+// Sum of the class counts (soft: the exact integer sum, rounded once).
+__device__ __forceinline__ float rec_count_sum(const float* r, int K, int layout) {
+  if (layout == kRecSoftFx) {
+    long long t = 0;
+    for (int k = 0; k < K; ++k) t += rec_fx(r)[2 + k];
+    return unfx32(t);
+  }
+  float t = 0.f;
+  for (int k = 0; k < K; ++k) t += r[2 * k + 1];
+  return t;
 }
 
 __device__ __forceinline__ uint64_t global_ns() {

@@ -29,7 +29,7 @@ __device__ __forceinline__ bool voxel_present(const MapView& mv, bool open, uint
     return r >= 0 && mv.tsdf[r].y > 0.f;
   }
   *row = -1;
-  return rec_weight(mv.rec + ((size_t)slot * kBlockVoxels + l) * mv.rs, mv.K, mv.split) > 0.f;
+  return rec_weight(mv.rec + ((size_t)slot * kBlockVoxels + l) * mv.rs, mv.K, mv.layout) > 0.f;
 }
 
 __global__ void __launch_bounds__(256) k_extract_count(MapView mv, const uint32_t* __restrict__ slots,
@@ -90,31 +90,21 @@ __global__ void __launch_bounds__(256) k_extract_write(MapView mv, const uint32_
       }
     } else if (!open) {
       const float* r = mv.rec + ((size_t)slot * kBlockVoxels + l) * mv.rs;
-      // one-hot records hold (S_k, c_k) pairs, soft records (S, W, c_k)
-      const float* cnt = mv.split ? r + 1 : r + kSoftCnt;
-      const int cs = mv.split ? 2 : 1;
-      float S = 0.f, W = 0.f;
-      if (mv.split) {
-        for (int k = 0; k < a.K; ++k) {
-          S += r[2 * k];
-          W += r[2 * k + 1];
-        }
-      } else {
-        S = r[0];
-        W = r[1];
-      }
-      if (a.D) a.D[o] = S / W;
+      // one-hot records hold (S_k, c_k) pairs, soft records fixed-point
+      // (S, W, c_k)
+      const int lay = mv.layout;
+      const float W = rec_weight(r, a.K, lay);
+      if (a.D) a.D[o] = rec_sdf(r, a.K, lay);
       if (a.W) a.W[o] = W;
       if (a.index) a.index[o] = (int32_t)(slot * kBlockVoxels + l);
       if (a.unc) {
         // Dir(alpha~), alpha~_i = alpha0 + c_i, A = sum alpha~:
         // Var theta_i = alpha~_i (A - alpha~_i) / (A^2 (A + 1)); entropy of p = alpha~ / A
-        float A = 0.f;
-        for (int k = 0; k < a.K; ++k) A += a.alpha0 + cnt[k * cs];
+        const float A = (float)a.K * a.alpha0 + rec_count_sum(r, a.K, lay);
         const float den = A * A * (A + 1.f);
         float H = 0.f;
         for (int k = 0; k < a.K; ++k) {
-          const float al = a.alpha0 + cnt[k * cs];
+          const float al = a.alpha0 + rec_count(r, k, lay);
           a.unc[o * (a.K + 1) + k] = al * (A - al) / den;
           const float p = al / A;
           if (p > 0.f) H -= p * logf(p);
@@ -123,12 +113,11 @@ __global__ void __launch_bounds__(256) k_extract_write(MapView mv, const uint32_
       }
       if (a.sem) {
         if (a.flags & SLIM_EXTRACT_POSTERIOR) {
-          float tsum = 0.f;
-          for (int k = 0; k < a.K; ++k) tsum += cnt[k * cs];
-          const float den = (float)a.K * a.alpha0 + tsum;
-          for (int k = 0; k < a.K; ++k) a.sem[o * a.K + k] = (a.alpha0 + cnt[k * cs]) / den;
+          const float den = (float)a.K * a.alpha0 + rec_count_sum(r, a.K, lay);
+          for (int k = 0; k < a.K; ++k)
+            a.sem[o * a.K + k] = (a.alpha0 + rec_count(r, k, lay)) / den;
         } else {
-          for (int k = 0; k < a.K; ++k) a.sem[o * a.K + k] = cnt[k * cs];
+          for (int k = 0; k < a.K; ++k) a.sem[o * a.K + k] = rec_count(r, k, lay);
         }
       }
     } else {

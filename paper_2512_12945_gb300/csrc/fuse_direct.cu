@@ -34,52 +34,6 @@ namespace slim {
 
 constexpr int kDirectThreads = 256;
 
-// Insert-or-find `key` in the map's hash; returns its slot, or kFailSlot
-// after raising a fault (capacity, timeout) on the map's sticky status.
-__device__ __forceinline__ uint32_t map_block_slot(const MapView& mv, uint64_t key) {
-  uint32_t h = entry_of(mv, key);
-  for (int pr = 0; pr < mv.max_probe; ++pr) {
-    const uint64_t cur = *(volatile uint64_t*)&mv.hkeys[h];
-    bool mine = false, found = cur == key;
-    if (!found && cur == kEmptyKey) {
-      const unsigned long long prev = atomicCAS((unsigned long long*)&mv.hkeys[h],
-                                                (unsigned long long)kEmptyKey,
-                                                (unsigned long long)key);
-      mine = prev == kEmptyKey;
-      found = prev == key;
-    }
-    if (mine) {
-      const uint32_t slot = atomicAdd(&mv.ctr[kCtrBlocks], 1u);
-      uint32_t v = kFailSlot;
-      if (slot >= mv.block_cap) {
-        raise_status(mv.ctr, kDevCapacity, 1);
-      } else {
-        mv.blk_key[slot] = key;
-        v = slot;
-      }
-      st_relaxed(&mv.hvals[h], v);
-      return v;
-    }
-    if (found) {
-      uint32_t v = ld_relaxed(&mv.hvals[h]);
-      if (v == kNoSlot) {
-        const uint64_t t0 = global_ns();
-        while ((v = ld_relaxed(&mv.hvals[h])) == kNoSlot) {
-          if (global_ns() - t0 > kCrossCtaWaitNs) {
-            raise_status(mv.ctr, kDevTimeout, 5);
-            return kFailSlot;
-          }
-          __nanosleep(100);
-        }
-      }
-      return v < mv.block_cap ? v : kFailSlot;
-    }
-    h = (h + 1) & mv.entry_mask;
-  }
-  raise_status(mv.ctr, kDevCapacity, 2);
-  return kFailSlot;
-}
-
 // MODE: 0 one-hot, 1 soft counts, 2 latest label; WT: observations carry
 // the weight w~ of the linear decay behind the surface instead of 1 (every
 // job of a launch has the launch's mode and weighting, so the per-pair loop
@@ -108,22 +62,15 @@ __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_con
     if (MODE == 0) {
       red_add_v2(r + 2 * cls, wd, wt);
     } else if (MODE == 1) {
-      // soft counts: (S, W) += (w~ d, w~) and c += w~ p, four classes per
-      // reduction
-      red_add_v2(r, wd, wt);
+      // soft counts: (S, W) += (w~ d, w~) and c += w~ p as exact 64-bit
+      // fixed-point sums (one integer reduction per field)
+      unsigned long long* q = reinterpret_cast<unsigned long long*>(r);
+      red_add_u64(q, fx32(wd));
+      red_add_u64(q + 1, WT ? fx32(wt) : (1ull << 32));
       const float* p = J.sem + (size_t)j * J.K;
-      for (int k = 0; k < J.K; k += 4) {
-        float a0 = __ldg(p + k);
-        float a1 = k + 1 < J.K ? __ldg(p + k + 1) : 0.f;
-        float a2 = k + 2 < J.K ? __ldg(p + k + 2) : 0.f;
-        float a3 = k + 3 < J.K ? __ldg(p + k + 3) : 0.f;
-        if (WT) {
-          a0 = __fmul_rn(wt, a0);
-          a1 = __fmul_rn(wt, a1);
-          a2 = __fmul_rn(wt, a2);
-          a3 = __fmul_rn(wt, a3);
-        }
-        red_add_v4(r + kSoftCnt + k, a0, a1, a2, a3);
+      for (int k = 0; k < J.K; ++k) {
+        const float a = WT ? __fmul_rn(wt, __ldg(p + k)) : __ldg(p + k);
+        red_add_u64(q + 2 + k, fx32(a));
       }
     } else {
       const unsigned long long stamp = ((unsigned long long)J.g.scan_no << 40) |

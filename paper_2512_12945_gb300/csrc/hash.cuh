@@ -48,4 +48,53 @@ __device__ __forceinline__ int64_t hash_insert(const MapView& mv, uint64_t key) 
   return -1;
 }
 
+// Insert-or-find `key` in the map's hash; returns its slot, or kFailSlot
+// after raising a fault (capacity, timeout) on the map's sticky status. A
+// created block's slot comes from the allocation counter and is published
+// with a relaxed store: the block pools are kept in their initial state
+// beyond the counter, so a reader needs nothing else from the creator.
+__device__ __forceinline__ uint32_t map_block_slot(const MapView& mv, uint64_t key) {
+  uint32_t h = entry_of(mv, key);
+  for (int pr = 0; pr < mv.max_probe; ++pr) {
+    const uint64_t cur = *(volatile uint64_t*)&mv.hkeys[h];
+    bool mine = false, found = cur == key;
+    if (!found && cur == kEmptyKey) {
+      const unsigned long long prev = atomicCAS((unsigned long long*)&mv.hkeys[h],
+                                                (unsigned long long)kEmptyKey,
+                                                (unsigned long long)key);
+      mine = prev == kEmptyKey;
+      found = prev == key;
+    }
+    if (mine) {
+      const uint32_t slot = atomicAdd(&mv.ctr[kCtrBlocks], 1u);
+      uint32_t v = kFailSlot;
+      if (slot >= mv.block_cap) {
+        raise_status(mv.ctr, kDevCapacity, 1);
+      } else {
+        mv.blk_key[slot] = key;
+        v = slot;
+      }
+      st_relaxed(&mv.hvals[h], v);
+      return v;
+    }
+    if (found) {
+      uint32_t v = ld_relaxed(&mv.hvals[h]);
+      if (v == kNoSlot) {
+        const uint64_t t0 = global_ns();
+        while ((v = ld_relaxed(&mv.hvals[h])) == kNoSlot) {
+          if (global_ns() - t0 > kCrossCtaWaitNs) {
+            raise_status(mv.ctr, kDevTimeout, 5);
+            return kFailSlot;
+          }
+          __nanosleep(100);
+        }
+      }
+      return v < mv.block_cap ? v : kFailSlot;
+    }
+    h = (h + 1) & mv.entry_mask;
+  }
+  raise_status(mv.ctr, kDevCapacity, 2);
+  return kFailSlot;
+}
+
 }  // namespace slim

@@ -12,8 +12,6 @@
 //   3. the pairs are sorted by voxel key (stable CTA radix sort) and reduced
 //      per voxel run with warp shuffles; one red.add per voxel (and per
 //      present class) goes to HBM instead of one atomic per pair.
-// k_traverse_alloc (the block-allocation pass on its own) serves the
-// open-set path, whose pair pass needs every slot published beforehand.
 //
 // Voxel records (AoS, rs floats, 16-byte aligned; layouts in common.cuh)
 // keep sums: S = W * D instead of D. With w~ = 1 the paper's running average
@@ -34,78 +32,6 @@ constexpr int kTileCap = 6144;        // (voxel, point) pairs per tile
 constexpr int kTblSize = 2048;        // tile block table (open addressing)
 constexpr int kMaxTileBlocks = 1024;  // distinct blocks per tile
 constexpr int kMaxBandBlocks = 8;     // distinct blocks per point band
-
-// ------------------------------------------------------------------ K1
-__device__ __forceinline__ void zero_block(const MapView& mv, uint32_t slot, bool open) {
-  const unsigned lane = lane_id();
-  if (open) {
-    int4* p = reinterpret_cast<int4*>(mv.vox_row + (size_t)slot * kBlockVoxels);
-    for (int k = lane; k < kBlockVoxels / 4; k += 32) p[k] = make_int4(-1, -1, -1, -1);
-  } else {
-    float4* p = reinterpret_cast<float4*>(mv.rec + (size_t)slot * kBlockVoxels * mv.rs);
-    const int n4 = kBlockVoxels * mv.rs / 4;
-    for (int k = lane; k < n4; k += 32) p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
-__global__ void __launch_bounds__(256) k_traverse_alloc(MapView mv, ScanGeom g,
-                                                        const float* __restrict__ pts,
-                                                        int64_t n, int open) {
-  __shared__ uint64_t kbuf[256][kMaxBandBlocks];
-  __shared__ uint32_t s_status;
-  if (threadIdx.x == 0) s_status = *(volatile uint32_t*)&mv.ctr[kCtrStatus];
-  __syncthreads();
-  if (s_status) return;
-  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  int cnt = 0;
-  if (j < n) {
-    Ray ry;
-    if (ray_setup_at(g, pts, j, ry)) {
-      uint64_t last = kEmptyKey;
-      ray_for_each(g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float) {
-        const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
-        if (kb != last) {
-          if (cnt < kMaxBandBlocks) kbuf[threadIdx.x][cnt] = kb;
-          ++cnt;
-          last = kb;
-        }
-      });
-    }
-  }
-  if (cnt > kMaxBandBlocks) {
-    raise_status(mv.ctr, kDevInternal, 3);
-    cnt = kMaxBandBlocks;
-  }
-  // per round: drop duplicate keys in the warp, the leaders insert in
-  // parallel, then the warp zeroes each new block and publishes its slot
-  const unsigned lane = lane_id();
-  const int maxc = __reduce_max_sync(0xFFFFFFFFu, cnt);
-  for (int r = 0; r < maxc; ++r) {
-    const bool has = r < cnt;
-    const uint64_t key = has ? kbuf[threadIdx.x][r] : kEmptyKey;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, (unsigned long long)key);
-    const bool leader = has && (int)lane == __ffs(peers) - 1;
-    const int64_t h = leader ? hash_insert(mv, key) : -1;
-    uint32_t slot = kNoSlot;
-    if (h >= 0) {
-      slot = atomicAdd(&mv.ctr[kCtrBlocks], 1u);
-      if (slot >= mv.block_cap) {
-        raise_status(mv.ctr, kDevCapacity, 1);
-        slot = kNoSlot;
-      } else {
-        mv.blk_key[slot] = key;
-      }
-    }
-    unsigned nm = __ballot_sync(0xFFFFFFFFu, slot != kNoSlot);
-    while (nm) {
-      const int src = __ffs(nm) - 1;
-      zero_block(mv, __shfl_sync(0xFFFFFFFFu, slot, src), open != 0);
-      nm &= nm - 1;
-    }
-    __syncwarp();
-    if (slot != kNoSlot) mv.hvals[h] = slot;
-  }
-}
 
 // ------------------------------------------------------------------ K2
 // Insert a block key into the tile's shared table; returns its entry.
@@ -355,42 +281,36 @@ __global__ void __launch_bounds__(256, 2)
       if (r && (int)lane == ldr) red_add_v2(r + 2 * cl, ws[lane], (float)__popc(pc));
       __syncwarp();
     } else {
+      // soft counts: exact 64-bit fixed-point sums of the run's d and
+      // probabilities (segmented over the window), one integer reduction
+      // per field from the run's first lane
       const unsigned peers = __match_any_sync(0xFFFFFFFFu, key2);
       const int first = __ffs(peers) - 1, lastl = 31 - __clz(peers);
-      float dsum = act ? pd[raw] : 0.f;
-      float cnt = act ? 1.f : 0.f;
+      unsigned long long* q = reinterpret_cast<unsigned long long*>(r);
+      unsigned long long dsum = act ? fx32(pd[raw]) : 0ull;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
-        const float a1 = __shfl_down_sync(0xFFFFFFFFu, dsum, off);
-        const float a2 = __shfl_down_sync(0xFFFFFFFFu, cnt, off);
-        if ((int)lane + off <= lastl) {
-          dsum += a1;
-          cnt += a2;
-        }
+        const unsigned long long a1 = __shfl_down_sync(0xFFFFFFFFu, dsum, off);
+        if ((int)lane + off <= lastl) dsum += a1;
       }
-      if (r && (int)lane == first) red_add_v2(r, dsum, cnt);
+      if (r && (int)lane == first) {
+        red_add_u64(q, dsum);
+        red_add_u64(q + 1, (unsigned long long)__popc(peers) << 32);
+      }
       for (int k = 0; k < K; ++k) {
-        float pv = act ? probs[pt * K + k] : 0.f;
+        unsigned long long pv = act ? fx32(probs[pt * K + k]) : 0ull;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-          const float a1 = __shfl_down_sync(0xFFFFFFFFu, pv, off);
+          const unsigned long long a1 = __shfl_down_sync(0xFFFFFFFFu, pv, off);
           if ((int)lane + off <= lastl) pv += a1;
         }
-        if (r && (int)lane == first) atomicAdd(r + kSoftCnt + k, pv);
+        if (r && (int)lane == first) red_add_u64(q + 2 + k, pv);
       }
     }
   }
 }
 
 // ------------------------------------------------------------------ launch
-cudaError_t launch_traverse_alloc(const MapView& mv, const ScanGeom& g, const float* pts,
-                                  int64_t n, bool open, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((n + 255) / 256);
-  k_traverse_alloc<<<grid, 256, 0, st>>>(mv, g, pts, n, open ? 1 : 0);
-  return cudaGetLastError();
-}
-
 cudaError_t closed_setup_attributes(int mode, int K, int tile_points) {
   const size_t sm = closed_smem_bytes(mode, K, tile_points);
   cudaError_t e = hash_setup_attributes();

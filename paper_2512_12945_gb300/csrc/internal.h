@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/slim_gb300.h"
@@ -10,8 +11,6 @@
 namespace slim {
 
 // integrate_closed.cu
-cudaError_t launch_traverse_alloc(const MapView& mv, const ScanGeom& g, const float* pts,
-                                  int64_t n, bool open, cudaStream_t st);
 cudaError_t launch_fuse_closed(const MapView& mv, const ScanGeom& g, const float* pts,
                                const float* sem, int64_t n, int mode, int K, int tile_points,
                                cudaStream_t st);
@@ -52,6 +51,52 @@ cudaError_t launch_fuse_hash(const MapView& mv, const ScanGeom& g, const float* 
 int hash_max_tile(int band_blocks);
 int closed_tile_points(int cap, int band_blocks);
 int max_band_blocks();
+
+// open.cu: open-set integration by tiles of pixels aggregated on chip.
+// Per-row accumulators of one integration call of a map:
+//   rows[row * stride]: {sum d (int64, unit 2^-32 m), n (u32), pad,
+//                        (S1, S2) for each of the L elements}
+struct OpenAcc {
+  float* rows;      // [row_cap * stride], zero between calls
+  uint32_t* listed; // [row_cap] 1 while the row is in list (cleared by the update)
+  uint32_t* list;   // [row_cap] rows touched by the current call
+  uint32_t* count;  // entries in list
+  int32_t stride;   // floats per accumulator row: 4 + 2 L
+};
+struct alignas(64) OpenJob {
+  CUtensorMap sem_map;  // the scan's embeddings as an L x n FP32 tensor
+  MapView mv;
+  ScanGeom g;
+  OpenAcc acc;
+  const float* pts;
+  const float* sem;
+  int64_t n;
+  int32_t L;
+  int32_t width;        // organized frames: pixels per image row; 0: unorganized
+  int32_t tw_log2;      // organized frames: log2 of the tile width (3, 4, 5)
+  uint32_t tiles_x;     // set by launch_open_tiles
+  uint32_t tile_begin;  // set by launch_open_tiles
+};
+constexpr int kMaxOpenJobs = 16;
+struct OpenBatch {
+  OpenJob job[kMaxOpenJobs];
+  int32_t n_jobs;
+  uint32_t total_tiles;
+};
+struct OpenApplyJob {
+  MapView mv;
+  OpenAcc acc;
+  int32_t L;
+};
+struct OpenApplyBatch {
+  OpenApplyJob job[kMaxOpenJobs];
+  int32_t n_jobs;
+};
+bool open_encode_sem(CUtensorMap* map, const float* sem, int64_t n, int L, int row_pts);
+cudaError_t launch_open_tiles(OpenBatch& b, int bf16, cudaStream_t st);
+cudaError_t launch_open_apply(const OpenApplyBatch& a, int bf16, cudaStream_t st);
+// Set the voxel-row tables of the blocks allocated so far back to -1.
+cudaError_t launch_reset_vox_rows(const MapView& mv, cudaStream_t st);
 
 // device_sort.cu: stable LSD radix sort of (key, value) pairs in global memory
 // over key bits [0, bits). keys/vals are sorted in place using the tmp

@@ -10,19 +10,11 @@ namespace slim {
 // Record a failure message for slim_last_error() and return s.
 slim_status fail(slim_status s, const std::string& msg);
 
-// Scratch of the open-set path, sized by max_points at map creation.
+// Scratch of the open-set path: per-row accumulators of one integration
+// call and the list of the rows it touched.
 struct OpenScratch {
-  int64_t pair_cap = 0;          // (voxel, point) pairs per scan
-  uint32_t* keys = nullptr;      // voxel key per pair (slot << 9 | local)
-  uint32_t* vals = nullptr;      // pair index, permuted with the keys
-  uint32_t* keys_tmp = nullptr;  // sort ping-pong buffers
-  uint32_t* vals_tmp = nullptr;
-  float* pair_d = nullptr;       // SDF of each pair, by pair index
-  uint32_t* pair_pt = nullptr;   // point of each pair, by pair index
-  float2* part = nullptr;        // per piece and side: (mean, M2) per element
-  uint4* meta = nullptr;         // per piece and side: (n, sum d, flags, key)
-  uint32_t* ctr = nullptr;       // device counters: pairs, runs
-  void* tmp = nullptr;           // sort / scan temp
+  OpenAcc acc{};
+  int32_t tw_log2 = 4;  // tile width of organized frames: 16 x 16 pixels (slim_autotune)
 };
 // Scratch of the open-set query.
 struct QueryScratch {
@@ -99,8 +91,8 @@ namespace slim {
 // prof_begin returns a token for prof_end (-1 when off).
 int prof_begin(slim_map* m, int kind, cudaStream_t st);
 void prof_end(slim_map* m, int token, cudaStream_t st);
-slim_status open_alloc_scratch(slim_map* m, OpenScratch& o, int64_t max_points);
-cudaError_t open_setup_attributes(slim_map* m);
+slim_status open_alloc_scratch(slim_map* m, OpenScratch& o);
+cudaError_t open_setup_attributes();
 cudaError_t query_setup_attributes();
 slim_status run_render(slim_map* m, const double world_from_camera[16], float fx, float fy,
                        float cx, float cy, int32_t width, int32_t height, float near_t,
@@ -112,7 +104,19 @@ slim_status run_backward(slim_map* m, const ScanGeom& g, const float* pts, const
 slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float temperature, float tp,
                       int32_t* label, float* prob, float* scores, uint32_t n_rows,
                       cudaStream_t st);
-slim_status open_integrate(slim_map* m, const MapView& mv, OpenScratch& o, const ScanGeom& g,
-                           const float* pts, const float* sem, int64_t n, int L, int bf16,
-                           cudaStream_t st);
+// Integrate one scan (or z-depth frame, g.depth set) of an open-set map:
+// width = pixels per image row of an organized frame, 0 for unorganized
+// points.
+slim_status open_integrate(slim_map* m, const ScanGeom& g, const float* pts, const float* sem,
+                           int64_t n, int width, cudaStream_t st);
+// One open-set item of a batched integration.
+struct OpenItem {
+  slim_map* map;
+  ScanGeom g;
+  const float* pts;
+  const float* sem;
+  int64_t n;
+  int width;
+};
+slim_status open_integrate_batch(const std::vector<OpenItem>& items, cudaStream_t st);
 }  // namespace slim

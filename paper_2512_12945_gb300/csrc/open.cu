@@ -1,128 +1,135 @@
 // Open-set scan integration (Sec. III-D): per voxel and per embedding element
 // the Normal-Inverse-Gamma update of Theorem 2 with lambda = W and nu = W / 2
 // (the implementation simplification of Sec. III-D), applied once per scan
-// to the scan's set of n observations of the voxel, in the form the theorem
-// states (Eqs. norm_update_1 and norm_update_4):
-//   zbar = batch mean,  M2 = sum (z - zbar)^2,  W' = W + n,
-//   m'    = (W m + n zbar) / W'            = m + (zbar - m) n / W'
-//   beta' = beta + M2 / 2 + (W n / W') (zbar - m)^2 / 2.
-// zbar and M2 of a run of observations are accumulated about its first
-// observation s (S1 = sum (z - s), S2 = sum (z - s)^2, zbar = s + S1 / n,
-// M2 = S2 - S1^2 / n), which keeps the sums small and free of cancellation;
-// runs longer than one piece are merged from per-piece statistics.
+// to the scan's set of n observations of the voxel. With every observation
+// taken about a shift vector s of the voxel (S1 = sum (z - s),
+// S2 = sum (z - s)^2, W' = W + n), Eqs. norm_update_1 and norm_update_4 read
+//   s = m (a voxel seen before):  m' = m + S1 / W',
+//                                 beta' = beta + (S2 - S1^2 / W') / 2;
+//   s = z_1 (a new voxel, W = 0): m' = s + S1 / n,
+//                                 beta' = (S2 - S1^2 / n) / 2,
+// the second being the batch mean and half the sum of squared deviations.
+// Both are sums over observations, so partial sums from any grouping of the
+// observations add up to the same update (Theorem 2 is stated for sets).
 //
-// Pipeline per scan (besides the shared block-allocation pass):
-//   k_open_pairs  band DDA per point; the point's distinct blocks are looked
-//                 up warp-cooperatively; every (voxel, point) pair is written
-//                 as key = slot << 9 | local, with its d and point index.
-//   radix sort    device-wide, by voxel key (count of pairs read on device).
-//   k_open_frag   one warp per piece of 64 sorted pairs: whole runs are
-//                 applied at once (the warp owns the voxel: state read once,
-//                 updated in FP32 registers, written once, f32 or bf16
-//                 storage, no atomics on records); runs cut by a piece
-//                 boundary leave per-piece statistics.
-//   k_open_merge  one warp per cut run: merge its pieces and apply.
+// Pipeline per integration call (pairs never reach HBM):
+//   k_open_tile   one CTA per tile of 16 x 16 pixels of an organized frame
+//                 (or 256 consecutive points): band DDA per pixel; the tile's
+//                 distinct voxels in a shared-memory table with a pixel mask,
+//                 count and fixed-point sum of d per voxel; blocks and voxel
+//                 rows looked up or created in the map (a new row gets its
+//                 shift, the embedding of one of its pixels, before it is
+//                 published); the embedding rows streamed in 64-element
+//                 chunks by TMA into shared memory, each read once from HBM;
+//                 per (voxel, chunk) one warp sums y = z - s and y^2 over the
+//                 voxel's pixels (packed FP32x2 arithmetic) and adds them to
+//                 the row's accumulator with one vector reduction per lane.
+//   k_open_apply  one warp per row the call touched: the update above from
+//                 the accumulator, the row's state read and written once,
+//                 the accumulator cleared.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "block_sort.cuh"
 #include "geometry.cuh"
 #include "hash.cuh"
 #include "map.h"
+#include "tma.cuh"
 
 namespace slim {
 
-constexpr int kOpenBandBlocks = 8;
-// device counters of the open-set scratch
-enum { kOpPairs = 0, kOpCounters = 4 };
+constexpr int kOT = 256;          // pixels per tile
+constexpr int kORowPts = 16;      // points per staged row of unorganized tiles
+constexpr int kOE = 64;           // embedding elements per staged chunk
+constexpr int kOMaxTV = 256;      // distinct voxels per tile part
+constexpr int kOTbl = 1024;       // voxel table entries (power of two)
+constexpr int kOThreads = 256;
+constexpr int32_t kPendingRow = -2;  // vox_row: being created by another CTA
+constexpr int32_t kFailRow = -3;     // vox_row: creation failed (capacity)
 
-__global__ void __launch_bounds__(256) k_open_pairs(MapView mv, ScanGeom g,
-                                                    const float* __restrict__ pts, int64_t n,
-                                                    uint32_t* keys, uint32_t* vals, float* pair_d,
-                                                    uint32_t* pair_pt, uint32_t* ctr,
-                                                    uint32_t pair_cap) {
-  __shared__ uint64_t kbuf[256][kOpenBandBlocks];
-  __shared__ uint32_t sbuf[256][kOpenBandBlocks];
-  __shared__ uint32_t s_status;
-  if (threadIdx.x == 0) s_status = *(volatile uint32_t*)&mv.ctr[kCtrStatus];
-  __syncthreads();
-  if (s_status) return;
-  const unsigned lane = lane_id();
-  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  int cnt = 0, np = 0;
-  Ray ry;
-  const bool valid = j < n && ray_setup_at(g, pts, j, ry);
-  if (valid) {
-    Ray r2 = ry;
-    uint64_t last = kEmptyKey;
-    ray_for_each(g, r2, [&](int32_t i0, int32_t i1, int32_t i2, float) {
-      const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
-      if (kb != last) {
-        if (cnt < kOpenBandBlocks) kbuf[threadIdx.x][cnt] = kb;
-        ++cnt;
-        last = kb;
-      }
-      ++np;
-    });
+// --------------------------------------------------------------- helpers
+__device__ __forceinline__ uint64_t pack_voxel(int32_t i0, int32_t i1, int32_t i2) {
+  return ((uint64_t)(uint32_t)(i0 + (1 << 20)) << 42) |
+         ((uint64_t)(uint32_t)(i1 + (1 << 20)) << 21) | (uint64_t)(uint32_t)(i2 + (1 << 20));
+}
+
+__device__ __forceinline__ void unpack_voxel(uint64_t k, int32_t& i0, int32_t& i1, int32_t& i2) {
+  i0 = (int32_t)((k >> 42) & 0x1FFFFF) - (1 << 20);
+  i1 = (int32_t)((k >> 21) & 0x1FFFFF) - (1 << 20);
+  i2 = (int32_t)(k & 0x1FFFFF) - (1 << 20);
+}
+
+// Packed FP32x2 arithmetic (each half rounded to nearest, as two scalar ops).
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t a) {
+  return make_float2(__uint_as_float((uint32_t)a), __uint_as_float((uint32_t)(a >> 32)));
+}
+__device__ __forceinline__ uint64_t f2_pack(float x, float y) {
+  return (uint64_t)__float_as_uint(x) | ((uint64_t)__float_as_uint(y) << 32);
+}
+
+__device__ __forceinline__ void red_add_v4_nc(float* r, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(r), "f"(a), "f"(b),
+               "f"(c), "f"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ void red_add_u32(uint32_t* a, uint32_t v) {
+  asm volatile("red.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int32_t ld_acquire_i32(const int32_t* p) {
+  return (int32_t)ld_acquire(reinterpret_cast<const uint32_t*>(p));
+}
+
+// TMA 2D load with an L2 evict-first policy: the embeddings are read once.
+__device__ __forceinline__ void tma_load_2d_stream(uint32_t dst, const CUtensorMap* map,
+                                                   int32_t x, int32_t y, uint32_t bar,
+                                                   uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+template <int BF16>
+__device__ __forceinline__ float2 load2(const void* base, size_t idx) {
+  if (BF16) {
+    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(
+        static_cast<const __nv_bfloat16*>(base) + idx);
+    return __bfloat1622float2(v);
   }
-  if (cnt > kOpenBandBlocks) {
-    raise_status(mv.ctr, kDevInternal, 10);
-    cnt = kOpenBandBlocks;
-    np = 0;
-  }
-  // lookups of the distinct blocks: duplicates dropped per warp, leaders
-  // probe in parallel and share the slot with their peers
-  const int maxc = __reduce_max_sync(0xFFFFFFFFu, cnt);
-  for (int r = 0; r < maxc; ++r) {
-    const bool has = r < cnt;
-    const uint64_t key = has ? kbuf[threadIdx.x][r] : kEmptyKey;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, (unsigned long long)key);
-    const int ldr = __ffs(peers) - 1;
-    uint32_t slot = kNoSlot;
-    if (has && (int)lane == ldr) slot = hash_find(mv, key);
-    slot = __shfl_sync(0xFFFFFFFFu, slot, ldr);
-    if (has) sbuf[threadIdx.x][r] = slot;
-  }
-  // positions: one atomic per warp
-  uint32_t x = (uint32_t)np;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
-    if ((int)lane >= off) x += y;
-  }
-  uint32_t base = 0;
-  if (lane == 31) base = atomicAdd(&ctr[kOpPairs], x);
-  base = __shfl_sync(0xFFFFFFFFu, base, 31) + x - (uint32_t)np;
-  if (valid && np > 0) {
-    if (base + (uint32_t)np > pair_cap) {
-      raise_status(mv.ctr, kDevCapacity, 11);
-      return;
-    }
-    uint64_t last = kEmptyKey;
-    int r = -1;
-    uint32_t k = 0;
-    ray_for_each(g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d) {
-      const uint64_t kb = pack_block(i0 >> 3, i1 >> 3, i2 >> 3);
-      if (kb != last) {
-        last = kb;
-        ++r;
-      }
-      const uint32_t slot = sbuf[threadIdx.x][r];
-      const uint32_t pos = base + k++;
-      keys[pos] = slot == kNoSlot ? 0xFFFFFFFFu : ((slot << 9) | (uint32_t)local_index(i0, i1, i2));
-      vals[pos] = pos;
-      pair_d[pos] = d;
-      pair_pt[pos] = (uint32_t)j;
-    });
-  }
+  return *reinterpret_cast<const float2*>(static_cast<const float*>(base) + idx);
 }
 
 template <int BF16>
 __device__ __forceinline__ float4 load4(const void* base, size_t idx) {
   if (BF16) {
     const uint2 u = *reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(base) + idx);
-    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
-    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
-    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
     return make_float4(fa.x, fa.y, fb.x, fb.y);
   }
   return *reinterpret_cast<const float4*>(static_cast<const float*>(base) + idx);
@@ -142,450 +149,623 @@ __device__ __forceinline__ void store4(void* base, size_t idx, float4 v) {
   }
 }
 
-// ---------------------------------------------------------------- apply
-// Sorted pairs are cut into pieces of kPiece consecutive pairs, one warp per
-// piece. A piece holds fragments (maximal runs of one voxel key). A fragment
-// that is a whole run is applied at once by its warp (exclusive owner of the
-// voxel for this scan). A fragment cut by a piece boundary leaves its
-// statistics (n, sum d, per element mean and M2) in a side slot of its
-// piece: side 0 for the fragment that began in an earlier piece, side 1 for
-// the fragment that goes on into the next one. k_open_merge then takes, for
-// every run that starts in a piece p and leaves it, the side-1 slot of p and
-// the side-0 slots of the following pieces up to the run's end, merges them
-// with the pairwise update of Chan, Golub and LeVeque (count, mean, M2;
-// compensated sums) and applies the run. No warp walks more than kPiece
-// observations, however many pixels a voxel collects in one frame.
-constexpr int kPiece = 64;
-enum { kFragValid = 1, kFragHead = 2, kFragEnd = 4 };
-
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, off);
-  return x;
+// Pixel p of local tile lt of a job: its point index, or -1 outside the
+// frame. Organized frames (width > 0): tiles of 2^tw_log2 x 256 / 2^tw_log2
+// pixels of the image, pixel p at row p >> tw_log2; else 256 consecutive
+// points.
+__device__ __forceinline__ int64_t tile_point(const OpenJob& J, uint32_t lt, int p) {
+  int64_t j;
+  if (J.width > 0) {
+    const uint32_t tx = lt % J.tiles_x, ty = lt / J.tiles_x;
+    const int32_t u = (int32_t)(tx << J.tw_log2) + (p & ((1 << J.tw_log2) - 1));
+    const int64_t v = ((int64_t)ty << (8 - J.tw_log2)) + (p >> J.tw_log2);
+    if (u >= J.width) return -1;
+    j = v * J.width + u;
+  } else {
+    j = (int64_t)lt * kOT + p;
+  }
+  return j < J.n ? j : -1;
 }
 
-// Point index of piece position k (lane k & 31 of pt0 / pt1).
-__device__ __forceinline__ uint32_t piece_pt(uint32_t pt0, uint32_t pt1, int k) {
-  return __shfl_sync(0xFFFFFFFFu, k < 32 ? pt0 : pt1, k & 31);
+// Points staged per row of a tile, and the first point of row r (that many
+// consecutive points are copied together).
+__device__ __forceinline__ int tile_row_len(const OpenJob& J) {
+  return J.width > 0 ? 1 << J.tw_log2 : kORowPts;
+}
+__device__ __forceinline__ int64_t tile_row_point(const OpenJob& J, uint32_t lt, int r) {
+  if (J.width > 0) {
+    const uint32_t tx = lt % J.tiles_x, ty = lt / J.tiles_x;
+    return (((int64_t)ty << (8 - J.tw_log2)) + r) * J.width + ((int64_t)tx << J.tw_log2);
+  }
+  return (int64_t)lt * kOT + (int64_t)r * kORowPts;
 }
 
-__device__ __forceinline__ float4 sem4(const float* __restrict__ sem, uint32_t pt, int L, int e,
-                                       bool on) {
-  return on ? *reinterpret_cast<const float4*>(sem + (size_t)pt * L + e)
-            : make_float4(0.f, 0.f, 0.f, 0.f);
+struct OpenTileSmem {
+  float stage[kOT * kOE];          // one chunk of every pixel's embedding
+  uint64_t tbl_key[kOTbl];         // voxel key table
+  uint16_t tbl_tv[kOTbl];          // table entry -> dense tile voxel
+  uint64_t tv_key[kOMaxTV];
+  unsigned long long tv_dq[kOMaxTV];  // sum of d, fixed point 2^-32 m
+  uint32_t tv_mask[kOMaxTV][kOT / 32];
+  uint32_t tv_n[kOMaxTV];
+  int32_t tv_row[kOMaxTV];
+  uint32_t tv_flag[kOMaxTV];       // 1: row created here, 2: wait for another CTA
+  uint16_t order[kOMaxTV];         // tile voxels by decreasing pixel count
+  uint32_t scan[kOThreads / 32];
+  uint32_t misc[2];                // 0 status, 1 table overflow
+  uint32_t rowmask;                // staged rows holding a valid pixel
+  int32_t parts[2 * 16];           // pending pixel ranges
+  unsigned long long bar;
+};
+
+// Insert a voxel key into the tile table; returns its entry, or -1 when the
+// table is full.
+__device__ __forceinline__ int tbl_insert(OpenTileSmem& s, uint64_t key) {
+  uint32_t h = (uint32_t)mix64(key) & (kOTbl - 1);
+  for (int it = 0; it < kOTbl; ++it) {
+    const uint64_t cur = *(volatile uint64_t*)&s.tbl_key[h];
+    if (cur == key) return (int)h;
+    if (cur == kEmptyKey) {
+      const unsigned long long prev = atomicCAS((unsigned long long*)&s.tbl_key[h],
+                                                (unsigned long long)kEmptyKey,
+                                                (unsigned long long)key);
+      if (prev == kEmptyKey || prev == key) return (int)h;
+    }
+    h = (h + 1) & (kOTbl - 1);
+  }
+  return -1;
 }
 
-// Batch mean and M2 of one fragment [fb, fe) for G groups of 4 elements
-// (e[g] = the lane's first element of group g), accumulated about the
-// fragment's first observation s (S1 = sum (z - s), S2 = sum (z - s)^2,
-// mean = s + S1 / n, M2 = S2 - S1^2 / n): one walk over the observations,
-// G independent 16-byte loads per observation, two observations per step.
-template <int G>
-__device__ __forceinline__ void frag_stats_g(const float* __restrict__ sem, int L, uint32_t pt0,
-                                             uint32_t pt1, int fb, int fe, const int (&e)[G],
-                                             const bool (&on)[G], float (&mean)[G][4],
-                                             float (&m2)[G][4]) {
-  float sh[G][4], s1[G][4], s2[G][4];
-  {
-    const uint32_t pf = piece_pt(pt0, pt1, fb);
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const float4 v = sem4(sem, pf, L, e[g], on[g]);
-      sh[g][0] = v.x; sh[g][1] = v.y; sh[g][2] = v.z; sh[g][3] = v.w;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) s1[g][q] = s2[g][q] = 0.f;
-    }
+__device__ __forceinline__ int tbl_find(const OpenTileSmem& s, uint64_t key) {
+  uint32_t h = (uint32_t)mix64(key) & (kOTbl - 1);
+  for (int it = 0; it < kOTbl; ++it) {
+    const uint64_t cur = s.tbl_key[h];
+    if (cur == key) return (int)h;
+    if (cur == kEmptyKey) return -1;
+    h = (h + 1) & (kOTbl - 1);
   }
-  int k = fb + 1;
-  for (; k + 1 < fe; k += 2) {
-    const uint32_t pa = piece_pt(pt0, pt1, k), pb = piece_pt(pt0, pt1, k + 1);
-    float4 za[G], zb[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      za[g] = sem4(sem, pa, L, e[g], on[g]);
-      zb[g] = sem4(sem, pb, L, e[g], on[g]);
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const float va[4] = {za[g].x, za[g].y, za[g].z, za[g].w};
-      const float vb[4] = {zb[g].x, zb[g].y, zb[g].z, zb[g].w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float ya = __fsub_rn(va[q], sh[g][q]);
-        const float yb = __fsub_rn(vb[q], sh[g][q]);
-        s1[g][q] = __fadd_rn(s1[g][q], __fadd_rn(ya, yb));
-        s2[g][q] = __fadd_rn(s2[g][q], __fadd_rn(__fmul_rn(ya, ya), __fmul_rn(yb, yb)));
-      }
-    }
-  }
-  if (k < fe) {
-    const uint32_t pa = piece_pt(pt0, pt1, k);
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const float4 z = sem4(sem, pa, L, e[g], on[g]);
-      const float va[4] = {z.x, z.y, z.z, z.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float ya = __fsub_rn(va[q], sh[g][q]);
-        s1[g][q] = __fadd_rn(s1[g][q], ya);
-        s2[g][q] = __fadd_rn(s2[g][q], __fmul_rn(ya, ya));
-      }
-    }
-  }
-  const float invn = __fdiv_rn(1.0f, (float)(fe - fb));
-#pragma unroll
-  for (int g = 0; g < G; ++g)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      mean[g][q] = __fadd_rn(sh[g][q], __fmul_rn(s1[g][q], invn));
-      m2[g][q] = fmaxf(__fsub_rn(s2[g][q], __fmul_rn(__fmul_rn(s1[g][q], s1[g][q]), invn)), 0.f);
-    }
+  return -1;
 }
 
-// Voxel row of key (slot << 9 | local), allocated on its first observation
-// by lane 0 (the calling warp owns the voxel for this scan); -1 on a
-// capacity fault.
-__device__ __forceinline__ int32_t voxel_row(const MapView& mv, uint32_t key, int* fresh) {
-  int32_t row = 0;
-  int fr = 0;
-  if (lane_id() == 0) {
-    int32_t* vr = mv.vox_row + (size_t)(key >> 9) * kBlockVoxels + (key & 511u);
-    row = *vr;
-    if (row < 0) {
-      const uint32_t r = atomicAdd(&mv.ctr[kCtrRows], 1u);
-      if (r >= mv.row_cap) {
-        raise_status(mv.ctr, kDevCapacity, 12);
-        row = -1;
-      } else {
-        row = (int32_t)r;
-        *vr = row;
-        fr = 1;
-      }
-    }
+// Issue the TMA copies of chunk c of the tile (its rows of consecutive
+// points x 64 elements) on the stage barrier.
+// Rows without a valid pixel (s.rowmask bit clear) are not copied: their
+// stage rows are never read.
+__device__ __forceinline__ void issue_chunk(OpenTileSmem& s, const OpenJob& J, uint32_t lt, int c,
+                                            uint64_t policy) {
+  const uint32_t bar = smem_u32(&s.bar);
+  const int rl = tile_row_len(J), nr = kOT / rl;
+  const uint32_t rm = s.rowmask;
+  mbar_expect_tx(bar, (uint32_t)__popc(rm) * (uint32_t)rl * kOE * 4u);
+  for (int r = 0; r < nr; ++r) {
+    const int64_t y = tile_row_point(J, lt, r);
+    if (!((rm >> r) & 1u)) continue;
+    tma_load_2d_stream(smem_u32(&s.stage[r * rl * kOE]), &J.sem_map, c * kOE, (int32_t)y, bar,
+                       policy);
   }
-  *fresh = __shfl_sync(0xFFFFFFFFu, fr, 0);
-  return __shfl_sync(0xFFFFFFFFu, row, 0);
-}
-
-// Theorem 2 update of elements [e, e + 4) of a row with the batch
-// statistics: m' = m + (zbar - m) n / W', beta' = beta + M2 / 2 +
-// (W n / W') (zbar - m)^2 / 2 (fm = n / W', fb = W n / W'). Returns the
-// partial |m'|^2 of the stored values.
-template <int BF16>
-__device__ __forceinline__ float nig_apply4(const MapView& mv, size_t rbase, int e, int fresh,
-                                            float fm, float fb, const float mean[4],
-                                            const float m2[4]) {
-  float4 m = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : load4<BF16>(mv.mrow, rbase + e);
-  float4 b = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : load4<BF16>(mv.brow, rbase + e);
-  float mv4[4] = {m.x, m.y, m.z, m.w}, bv4[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const float d = mean[q] - mv4[q];
-    bv4[q] += 0.5f * (m2[q] + fb * d * d);
-    mv4[q] += d * fm;
-  }
-  m = make_float4(mv4[0], mv4[1], mv4[2], mv4[3]);
-  b = make_float4(bv4[0], bv4[1], bv4[2], bv4[3]);
-  store4<BF16>(mv.mrow, rbase + e, m);
-  store4<BF16>(mv.brow, rbase + e, b);
-  if (BF16) m = load4<BF16>(mv.mrow, rbase + e);  // norm of the stored values
-  return m.x * m.x + m.y * m.y + m.z * m.z + m.w * m.w;
 }
 
 template <int BF16>
-__global__ void __launch_bounds__(256) k_open_frag(MapView mv, const uint32_t* __restrict__ keys,
-                                                   const uint32_t* __restrict__ vals,
-                                                   const float* __restrict__ pair_d,
-                                                   const uint32_t* __restrict__ pair_pt,
-                                                   const uint32_t* __restrict__ ctr,
-                                                   const float* __restrict__ sem, int L,
-                                                   int64_t n_max, float2* part, uint4* meta) {
-  if (*(volatile uint32_t*)&mv.ctr[kCtrStatus]) return;
-  const unsigned lane = lane_id();
-  const int64_t n = min(n_max, (int64_t)ctr[kOpPairs]);
-  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t base = p * kPiece;
-  if (base >= n) return;
-  const int m = (int)(n - base < kPiece ? n - base : (int64_t)kPiece);
-  constexpr uint32_t kInv = 0xFFFFFFFFu;
-  const int64_t i0 = base + lane, i1 = base + 32 + lane;
-  const uint32_t key0 = (int)lane < m ? keys[i0] : kInv;
-  const uint32_t key1 = 32 + (int)lane < m ? keys[i1] : kInv;
-  uint32_t pt0 = 0, pt1 = 0;
-  float d0 = 0.f, d1 = 0.f;
-  if (key0 != kInv) {
-    const uint32_t v = vals[i0];
-    pt0 = pair_pt[v];
-    d0 = pair_d[v];
+__global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constant__ OpenBatch b) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  OpenTileSmem& s = *reinterpret_cast<OpenTileSmem*>(smraw);
+  const uint32_t t = blockIdx.x;
+  int jb = 0;
+  while (jb + 1 < b.n_jobs && t >= b.job[jb + 1].tile_begin) ++jb;
+  const OpenJob& J = b.job[jb];
+  const MapView& mv = J.mv;
+  const uint32_t lt = t - J.tile_begin;
+  const int tid = threadIdx.x;
+  const unsigned lane = lane_id(), warp = tid >> 5;
+  const int L = J.L;
+  const int nch = L / kOE;
+  const uint32_t bar = smem_u32(&s.bar);
+  uint64_t policy = 0;
+  if (tid == 0) {
+    s.misc[0] = *(volatile uint32_t*)&mv.ctr[kCtrStatus];
+    s.parts[0] = 0;  // the first part: the whole tile
+    s.parts[1] = kOT;
+    s.rowmask = 0u;
+    mbar_init(bar, 1);
+    mbar_fence_init();
   }
-  if (key1 != kInv) {
-    const uint32_t v = vals[i1];
-    pt1 = pair_pt[v];
-    d1 = pair_d[v];
+  __syncthreads();
+  if (s.misc[0]) return;
+  // this thread's pixel and ray; the staged rows that hold a valid pixel
+  const int64_t pj = tid < kOT ? tile_point(J, lt, tid) : -1;
+  Ray ray0;
+  const bool valid = pj >= 0 && ray_setup_at(J.g, J.pts, pj, ray0);
+  if (valid) atomicOr(&s.rowmask, 1u << (tid / tile_row_len(J)));
+  __syncthreads();
+  // chunk 0 is fetched while the rays are walked (it serves every part)
+  int cur = 0;          // chunk held or in flight in the stage
+  bool inflight = true;
+  uint32_t phase = 0;   // parity of the next completion of the stage barrier
+  if (tid == 0) {
+    policy = evict_first_policy();
+    issue_chunk(s, J, lt, 0, policy);
   }
-  const uint32_t prev_key = base > 0 ? keys[base - 1] : kInv;
-  const uint32_t next_key = base + kPiece < n ? keys[base + kPiece] : kInv;
-  // fragment starts as a 64-bit mask over the piece positions
-  const uint32_t up0 = __shfl_up_sync(0xFFFFFFFFu, key0, 1);
-  const uint32_t up1 = __shfl_up_sync(0xFFFFFFFFu, key1, 1);
-  const uint32_t last0 = __shfl_sync(0xFFFFFFFFu, key0, 31);
-  const bool st0 = lane == 0 || key0 != up0;
-  const bool st1 = lane == 0 ? key1 != last0 : key1 != up1;
-  const uint64_t smask = (uint64_t)__ballot_sync(0xFFFFFFFFu, st0) |
-                         ((uint64_t)__ballot_sync(0xFFFFFFFFu, st1) << 32);
-  if (lane == 0) meta[2 * p + 1] = make_uint4(0u, 0u, 0u, 0u);
-  int fb = 0;
-  while (fb < m) {
-    const uint64_t rest = fb < 63 ? (smask >> (fb + 1)) << (fb + 1) : 0ull;
-    const int fe = rest ? min(m, __ffsll((long long)rest) - 1) : m;
-    const uint32_t key = __shfl_sync(0xFFFFFFFFu, fb < 32 ? key0 : key1, fb & 31);
-    if (key == kInv) break;  // pairs without a block sort last
-    const bool before = fb == 0 && prev_key == key;
-    const bool after = fe == kPiece && next_key == key;
-    float sd = 0.f;
-    if ((int)lane >= fb && (int)lane < fe) sd += d0;
-    if (32 + (int)lane >= fb && 32 + (int)lane < fe) sd += d1;
-    sd = warp_sum(sd);
-    const int nf = fe - fb;
-    if (!before && !after) {  // a whole run: apply now
-      int fresh = 0;
-      const int32_t row = voxel_row(mv, key, &fresh);
-      if (row >= 0) {
-        const float2 sw = fresh ? make_float2(0.f, 0.f) : mv.tsdf[row];
-        const float Wn = sw.y + (float)nf;
-        const float fm = (float)nf / Wn, fbw = sw.y * (float)nf / Wn;
-        const size_t rbase = (size_t)row * L;
-        float nrm = 0.f;
-        for (int c0 = 0; c0 < L; c0 += 512) {
-          int e[4];
-          bool on[4];
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            e[g] = c0 + 128 * g + 4 * (int)lane;
-            on[g] = e[g] < L;
-          }
-          float mean[4][4], m2[4][4];
-          frag_stats_g<4>(sem, L, pt0, pt1, fb, fe, e, on, mean, m2);
-#pragma unroll
-          for (int g = 0; g < 4; ++g)
-            if (on[g]) nrm += nig_apply4<BF16>(mv, rbase, e[g], fresh, fm, fbw, mean[g], m2[g]);
-        }
-        nrm = warp_sum(nrm);
-        if (lane == 0) {
-          mv.tsdf[row] = make_float2(sw.x + sd, Wn);
-          mv.mnorm2[row] = nrm;
-        }
-      }
-    } else {  // cut by a piece boundary: leave the statistics for the merge
-      const int side = before ? 0 : 1;
-      const uint32_t flags = kFragValid | (before ? 0u : (uint32_t)kFragHead) |
-                             (after ? 0u : (uint32_t)kFragEnd);
-      float2* dst = part + (size_t)(2 * p + side) * L;
-      for (int c0 = 0; c0 < L; c0 += 512) {
-        int e[4];
-        bool on[4];
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          e[g] = c0 + 128 * g + 4 * (int)lane;
-          on[g] = e[g] < L;
-        }
-        float mean[4][4], m2[4][4];
-        frag_stats_g<4>(sem, L, pt0, pt1, fb, fe, e, on, mean, m2);
-#pragma unroll
-        for (int g = 0; g < 4; ++g)
-          if (on[g]) {
-            float4* d4 = reinterpret_cast<float4*>(dst + e[g]);
-            d4[0] = make_float4(mean[g][0], m2[g][0], mean[g][1], m2[g][1]);
-            d4[1] = make_float4(mean[g][2], m2[g][2], mean[g][3], m2[g][3]);
-          }
-      }
-      if (lane == 0) meta[2 * p + side] = make_uint4((uint32_t)nf, __float_as_uint(sd), flags, key);
-    }
-    fb = fe;
-  }
-}
 
-// One warp per run that leaves the piece it starts in: merge its fragments
-// (side 1 of the head piece, side 0 of the following pieces up to the
-// fragment flagged as the run's end) and apply the run. A voxel close to
-// the sensor can collect thousands of observations in one frame, so a run
-// can span tens of pieces: the run's end is searched 32 pieces per step
-// (one piece metadata word per lane) and the fragments' statistics are
-// loaded kMergeAhead pieces at a time, so the warp's chain of dependent
-// loads grows with the run length / kMergeAhead, not with the run length.
-constexpr int kMergeAhead = 6;
-
-template <int BF16>
-__global__ void __launch_bounds__(256, 2) k_open_merge(MapView mv, const uint32_t* __restrict__ ctr,
-                                                    int L, int64_t n_max,
-                                                    const float2* __restrict__ part,
-                                                    const uint4* __restrict__ meta) {
-  if (*(volatile uint32_t*)&mv.ctr[kCtrStatus]) return;
-  const unsigned lane = lane_id();
-  const int64_t n = min(n_max, (int64_t)ctr[kOpPairs]);
-  const int64_t np = (n + kPiece - 1) / kPiece;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < np; p += warps) {
-    const uint4 h = meta[2 * p + 1];
-    if (!(h.z & kFragHead)) continue;
-    const uint32_t key = h.w;
-    // the chain of pieces after p: count, sum d and the end piece
-    float ntot = 0.f, sd = 0.f;
-    int64_t q_end = -1;
-    for (int64_t b0 = p + 1; b0 < np; b0 += 32) {
-      const int64_t q = b0 + (int64_t)lane;
-      const uint4 t = q < np ? meta[2 * q] : make_uint4(0u, 0u, 0u, 0u);
-      const bool same = (t.z & kFragValid) && t.w == key;
-      const unsigned brk = __ballot_sync(0xFFFFFFFFu, !same);
-      const unsigned end = __ballot_sync(0xFFFFFFFFu, same && (t.z & kFragEnd));
-      const int nb = brk ? __ffs(brk) - 1 : 32;  // first lane outside the chain
-      const int ne = end ? __ffs(end) - 1 : 32;  // first lane holding the end
-      const int take = ne < nb ? ne + 1 : nb;
-      ntot += warp_sum((int)lane < take ? (float)t.x : 0.f);
-      sd += warp_sum((int)lane < take ? __uint_as_float(t.y) : 0.f);
-      if (ne < nb) {
-        q_end = b0 + ne;
-        break;
-      }
-      if (nb < 32) break;
+  int nparts = 1;
+  bool abort = false;
+  while (nparts > 0 && !abort) {
+    --nparts;
+    const int p0 = s.parts[2 * nparts], p1 = s.parts[2 * nparts + 1];
+    const bool mine = valid && tid >= p0 && tid < p1;
+    // 1. the part's distinct voxels
+    for (int e = tid; e < kOTbl; e += kOThreads) s.tbl_key[e] = kEmptyKey;
+    if (tid == 0) s.misc[1] = 0;
+    __syncthreads();
+    if (mine) {
+      Ray ry = ray0;
+      ray_for_each(J.g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float) {
+        if (tbl_insert(s, pack_voxel(i0, i1, i2)) < 0) s.misc[1] = 1;
+      });
     }
-    if (q_end < 0) {  // consistency check, never expected
-      if (lane == 0) raise_status(mv.ctr, kDevInternal, 13);
+    __syncthreads();
+    // 2. dense ids (4 table entries per thread)
+    uint32_t occ = 0;
+#pragma unroll
+    for (int k = 0; k < kOTbl / kOThreads; ++k) occ += s.tbl_key[tid * 4 + k] != kEmptyKey;
+    uint32_t ntv;
+    uint32_t off = cta_exclusive_scan(occ, s.scan, &ntv);
+    if (ntv > (uint32_t)kOMaxTV || s.misc[1]) {
+      // too many voxels for the tables: split the part in two
+      __syncthreads();
+      if (tid == 0) {
+        const int mid = (p0 + p1) / 2;
+        s.parts[2 * nparts] = p0;
+        s.parts[2 * nparts + 1] = mid;
+        s.parts[2 * nparts + 2] = mid;
+        s.parts[2 * nparts + 3] = p1;
+      }
+      nparts += 2;
+      __syncthreads();
       continue;
     }
-    ntot += (float)h.x;
-    sd += __uint_as_float(h.y);
-    int fresh = 0;
-    const int32_t row = voxel_row(mv, key, &fresh);
-    if (row < 0) continue;
-    const float2 sw = fresh ? make_float2(0.f, 0.f) : mv.tsdf[row];
-    const float Wn = sw.y + ntot;
-    const float fm = ntot / Wn, fbw = sw.y * ntot / Wn;
-    const size_t rbase = (size_t)row * L;
-    float nrm = 0.f;
-    for (int c0 = 0; c0 < L; c0 += 128) {
-      const int e = c0 + 4 * (int)lane;
-      if (e >= L) continue;
-      float na = (float)h.x;
-      float mean[4], m2[4], mc[4] = {0.f, 0.f, 0.f, 0.f}, vc[4] = {0.f, 0.f, 0.f, 0.f};
-      {
-        const float4* s4 = reinterpret_cast<const float4*>(part + (size_t)(2 * p + 1) * L + e);
-        const float4 a = s4[0], b = s4[1];
-        mean[0] = a.x; m2[0] = a.y; mean[1] = a.z; m2[1] = a.w;
-        mean[2] = b.x; m2[2] = b.y; mean[3] = b.z; m2[3] = b.w;
-      }
-      for (int64_t r0 = p + 1; r0 <= q_end; r0 += kMergeAhead) {
-        float nbv[kMergeAhead];
-        float4 av[kMergeAhead], bv[kMergeAhead];
 #pragma unroll
-        for (int u = 0; u < kMergeAhead; ++u) {
-          const int64_t r = r0 + u;
-          if (r <= q_end) {
-            nbv[u] = (float)meta[2 * r].x;
-            const float4* s4 = reinterpret_cast<const float4*>(part + (size_t)(2 * r) * L + e);
-            av[u] = s4[0];
-            bv[u] = s4[1];
+    for (int k = 0; k < kOTbl / kOThreads; ++k) {
+      const int e = tid * 4 + k;
+      const uint64_t key = s.tbl_key[e];
+      if (key != kEmptyKey) {
+        s.tbl_tv[e] = (uint16_t)off;
+        s.tv_key[off] = key;
+        ++off;
+      }
+    }
+    for (int v = tid; v < (int)ntv; v += kOThreads) {
+      s.tv_n[v] = 0;
+      s.tv_dq[v] = 0ull;
+      s.tv_flag[v] = 0;
+#pragma unroll
+      for (int w = 0; w < kOT / 32; ++w) s.tv_mask[v][w] = 0u;
+    }
+    __syncthreads();
+    // 3. pixel masks, counts and fixed-point sums of d
+    if (mine) {
+      Ray ry = ray0;
+      ray_for_each(J.g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d) {
+        const int e = tbl_find(s, pack_voxel(i0, i1, i2));
+        const int v = s.tbl_tv[e];
+        atomicOr(&s.tv_mask[v][tid >> 5], 1u << (tid & 31));
+        atomicAdd(&s.tv_n[v], 1u);
+        atomicAdd(&s.tv_dq[v], fx32(d));
+      });
+    }
+    __syncthreads();
+    // 4. blocks and rows: find, or create (a new row gets its shift and
+    //    zero (S, W) before it is published), or wait for another CTA's
+    int32_t* vr = nullptr;
+    if (tid < (int)ntv) {
+      int32_t i0, i1, i2;
+      unpack_voxel(s.tv_key[tid], i0, i1, i2);
+      const uint32_t slot = map_block_slot(mv, pack_block(i0 >> 3, i1 >> 3, i2 >> 3));
+      int32_t row = kFailRow;
+      if (slot < mv.block_cap) {
+        vr = mv.vox_row + (size_t)slot * kBlockVoxels + local_index(i0, i1, i2);
+        const int32_t r0 = atomicCAS(vr, -1, kPendingRow);
+        if (r0 == -1) {
+          const uint32_t r = atomicAdd(&mv.ctr[kCtrRows], 1u);
+          if (r >= mv.row_cap) {
+            raise_status(mv.ctr, kDevCapacity, 12);
+            st_release(reinterpret_cast<uint32_t*>(vr), (uint32_t)kFailRow);
+          } else {
+            row = (int32_t)r;
+            s.tv_flag[tid] = 1;
+          }
+        } else if (r0 == kPendingRow) {
+          s.tv_flag[tid] = 2;
+        } else if (r0 >= 0) {
+          row = r0;
+        }
+      }
+      s.tv_row[tid] = row;
+    }
+    __syncthreads();
+    // the shift of each row created here: the embedding of its first pixel
+    for (int v = (int)warp; v < (int)ntv; v += kOThreads / 32) {
+      if (s.tv_flag[v] != 1) continue;
+      int p = 0;
+      for (int w = 0; w < kOT / 32; ++w)
+        if (s.tv_mask[v][w]) {
+          p = 32 * w + __ffs(s.tv_mask[v][w]) - 1;
+          break;
+        }
+      const int64_t jp = tile_point(J, lt, p);
+      const int32_t row = s.tv_row[v];
+      const float* src = J.sem + (size_t)jp * L;
+      for (int e = 4 * (int)lane; e < L; e += 128)
+        store4<BF16>(mv.mrow, (size_t)row * L + e, *reinterpret_cast<const float4*>(src + e));
+      if (lane == 0) mv.tsdf[row] = make_float2(0.f, 0.f);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid < (int)ntv) {
+      if (s.tv_flag[tid] == 1) {
+        st_release(reinterpret_cast<uint32_t*>(vr), (uint32_t)s.tv_row[tid]);
+      } else if (s.tv_flag[tid] == 2) {
+        int32_t r = ld_acquire_i32(vr);
+        if (r == kPendingRow) {
+          const uint64_t t0 = global_ns();
+          while ((r = ld_acquire_i32(vr)) == kPendingRow) {
+            if (global_ns() - t0 > kCrossCtaWaitNs) {
+              raise_status(mv.ctr, kDevTimeout, 14);
+              r = kFailRow;
+              break;
+            }
+            __nanosleep(100);
           }
         }
-#pragma unroll
-        for (int u = 0; u < kMergeAhead; ++u) {
-          if (r0 + u > q_end) break;
-          const float nb = nbv[u];
-          const float mb[4] = {av[u].x, av[u].z, bv[u].x, bv[u].z};
-          const float vb[4] = {av[u].y, av[u].w, bv[u].y, bv[u].w};
-          const float nn = na + nb;
-          const float wb = nb / nn, wab = na * nb / nn;
+        s.tv_row[tid] = r >= 0 ? r : kFailRow;
+      }
+      const int32_t row = s.tv_row[tid];
+      if (row >= 0 && atomicExch(&J.acc.listed[row], 1u) == 0u)
+        J.acc.list[atomicAdd(J.acc.count, 1u)] = (uint32_t)row;
+      // rank by decreasing pixel count (ties by id): the longest voxels first
+      const uint32_t n0 = s.tv_n[tid];
+      int rank = 0;
+      for (int v = 0; v < (int)ntv; ++v) {
+        const uint32_t nv = s.tv_n[v];
+        rank += nv > n0 || (nv == n0 && v < tid);
+      }
+      s.order[rank] = (uint16_t)tid;
+    }
+    __syncthreads();
+    // 5. per chunk: sums of y = z - s and y^2 over each voxel's pixels
+    for (int c = 0; c < nch; ++c) {
+      if (cur != c) {  // the stage is free (barrier at the end of the last chunk)
+        if (tid == 0) issue_chunk(s, J, lt, c, policy);
+        cur = c;
+        inflight = true;
+      }
+      if (inflight) {
+        const bool ok = mbar_wait(bar, phase);
+        if (__syncthreads_or(!ok)) {  // a copy that never landed: stop, uniformly
+          if (tid == 0) raise_status(mv.ctr, kDevTimeout, 15);
+          abort = true;
+          break;
+        }
+        phase ^= 1u;
+        inflight = false;
+      }
+      const int e0 = c * kOE + 2 * (int)lane;
+      for (int k = (int)warp; k < (int)ntv; k += kOThreads / 32) {
+        const int v = s.order[k];
+        const int32_t row = s.tv_row[v];
+        if (row < 0) continue;
+        const float2 sh = load2<BF16>(mv.mrow, (size_t)row * L + e0);
+        const uint64_t s2 = f2_pack(sh.x, sh.y);
+        uint64_t a1 = 0, a2 = 0, b1 = 0, b2 = 0;
+#pragma unroll 1
+        for (int w = 0; w < kOT / 32; ++w) {
+          uint32_t mk = s.tv_mask[v][w];
+          while (mk) {
+            const int pa = 32 * w + __ffs(mk) - 1;
+            mk &= mk - 1;
+            const uint64_t za = *reinterpret_cast<const uint64_t*>(&s.stage[pa * kOE + 2 * lane]);
+            const uint64_t ya = f2_sub(za, s2);
+            a1 = f2_add(a1, ya);
+            a2 = f2_fma(ya, ya, a2);
+            if (mk) {
+              const int pb = 32 * w + __ffs(mk) - 1;
+              mk &= mk - 1;
+              const uint64_t zb =
+                  *reinterpret_cast<const uint64_t*>(&s.stage[pb * kOE + 2 * lane]);
+              const uint64_t yb = f2_sub(zb, s2);
+              b1 = f2_add(b1, yb);
+              b2 = f2_fma(yb, yb, b2);
+            }
+          }
+        }
+        const float2 S1 = f2_unpack(f2_add(a1, b1)), S2 = f2_unpack(f2_add(a2, b2));
+        red_add_v4_nc(J.acc.rows + (size_t)row * J.acc.stride + 4 + 2 * e0, S1.x, S2.x, S1.y,
+                      S2.y);
+      }
+      __syncthreads();  // the stage is free again
+    }
+    if (abort) break;
+    // 6. counts and sums of d
+    if (tid < (int)ntv) {
+      const int32_t row = s.tv_row[tid];
+      if (row >= 0) {
+        float* h = J.acc.rows + (size_t)row * J.acc.stride;
+        red_add_u64(reinterpret_cast<unsigned long long*>(h), s.tv_dq[tid]);
+        red_add_u32(reinterpret_cast<uint32_t*>(h) + 2, s.tv_n[tid]);
+      }
+    }
+    __syncthreads();
+  }
+  if (abort && inflight) mbar_wait(bar, phase);  // let the copy land (bounded)
+}
+
+// Apply the accumulated statistics to every row the call touched (one warp
+// per row), then clear the accumulators and the rows' list flags. With the
+// map's status raised the rows are only cleared.
+template <int BF16>
+__global__ void __launch_bounds__(256) k_open_apply(const __grid_constant__ OpenApplyBatch b) {
+  const unsigned lane = lane_id();
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int jb = 0; jb < b.n_jobs; ++jb) {
+    const MapView& mv = b.job[jb].mv;
+    const OpenAcc& A = b.job[jb].acc;
+    const int L = b.job[jb].L;
+    const bool live = *(volatile uint32_t*)&mv.ctr[kCtrStatus] == 0;
+    const int64_t cnt = min((int64_t)*A.count, (int64_t)mv.row_cap);
+    for (int64_t i = gw; i < cnt; i += nw) {
+      const uint32_t row = A.list[i];
+      float* h = A.rows + (size_t)row * A.stride;
+      if (lane == 0) A.listed[row] = 0u;
+      if (live) {
+        const long long dq = *reinterpret_cast<const long long*>(h);
+        const uint32_t n = reinterpret_cast<const uint32_t*>(h)[2];
+        const float2 sw = mv.tsdf[row];
+        const float Wn = sw.y + (float)n;
+        const float inv = 1.0f / Wn;
+        const bool seen = sw.y > 0.f;
+        const size_t rb = (size_t)row * L;
+        float nrm = 0.f;
+        for (int e = 4 * (int)lane; e < L; e += 128) {
+          float4* a4 = reinterpret_cast<float4*>(h + 4 + 2 * e);
+          const float4 p = a4[0], q = a4[1];  // (S1, S2) of elements e .. e + 3
+          const float s1[4] = {p.x, p.z, q.x, q.z}, s2[4] = {p.y, p.w, q.y, q.w};
+          const float4 m4 = load4<BF16>(mv.mrow, rb + e);
+          const float4 b4 = seen ? load4<BF16>(mv.brow, rb + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+          float mv4[4] = {m4.x, m4.y, m4.z, m4.w}, bv4[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const float dl = mb[k] - mean[k];
-            // mean += dl * nb / n and M2 += M2_b + dl^2 na nb / n, compensated
-            const float ym = __fsub_rn(__fmul_rn(dl, wb), mc[k]);
-            const float tm = __fadd_rn(mean[k], ym);
-            mc[k] = __fsub_rn(__fsub_rn(tm, mean[k]), ym);
-            mean[k] = tm;
-            const float yv = __fsub_rn(__fadd_rn(vb[k], __fmul_rn(__fmul_rn(dl, dl), wab)), vc[k]);
-            const float tv = __fadd_rn(m2[k], yv);
-            vc[k] = __fsub_rn(__fsub_rn(tv, m2[k]), yv);
-            m2[k] = tv;
+            bv4[k] += 0.5f * fmaxf(s2[k] - s1[k] * s1[k] * inv, 0.f);
+            mv4[k] += s1[k] * inv;
           }
-          na = nn;
+          float4 mo = make_float4(mv4[0], mv4[1], mv4[2], mv4[3]);
+          store4<BF16>(mv.mrow, rb + e, mo);
+          store4<BF16>(mv.brow, rb + e, make_float4(bv4[0], bv4[1], bv4[2], bv4[3]));
+          if (BF16) mo = load4<BF16>(mv.mrow, rb + e);  // norm of the stored values
+          nrm += mo.x * mo.x + mo.y * mo.y + mo.z * mo.z + mo.w * mo.w;
+          a4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+          a4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xFFFFFFFFu, nrm, off);
+        if (lane == 0) {
+          mv.tsdf[row] = make_float2(sw.x + unfx32(dq), Wn);
+          mv.mnorm2[row] = nrm;
+          reinterpret_cast<float4*>(h)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      } else {
+        for (int e = 4 * (int)lane; e < 2 * L + 4; e += 128)
+          *reinterpret_cast<float4*>(h + e) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      nrm += nig_apply4<BF16>(mv, rbase, e, fresh, fm, fbw, mean, m2);
-    }
-    nrm = warp_sum(nrm);
-    if (lane == 0) {
-      mv.tsdf[row] = make_float2(sw.x + sd, Wn);
-      mv.mnorm2[row] = nrm;
     }
   }
 }
 
-slim_status open_alloc_scratch(slim_map* m, OpenScratch& o, int64_t max_points) {
-  const int64_t cap = std::max<int64_t>(1, max_points) * m->cap;
-  if (cap > (int64_t)0xFFFFFFF0ll) return fail(SLIM_ERR_ARG, "max_points * band cap too large");
-  o.pair_cap = cap;
+// ------------------------------------------------------------------ host
+size_t open_tile_smem_bytes() { return sizeof(OpenTileSmem) + 1024; }
+
+cudaError_t open_setup_attributes() {
+  const int sm = (int)open_tile_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(k_open_tile<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_open_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
+}
+
+slim_status open_alloc_scratch(slim_map* m, OpenScratch& o) {
+  const uint64_t rc = (uint64_t)m->p.voxel_capacity;
+  o.acc.stride = 4 + 2 * m->L;
   slim_status s;
-  if ((s = m->alloc(&o.keys, (size_t)cap)) != SLIM_OK) return s;
-  if ((s = m->alloc(&o.vals, (size_t)cap)) != SLIM_OK) return s;
-  if ((s = m->alloc(&o.keys_tmp, (size_t)cap)) != SLIM_OK) return s;
-  if ((s = m->alloc(&o.vals_tmp, (size_t)cap)) != SLIM_OK) return s;
-  if ((s = m->alloc(&o.pair_d, (size_t)cap)) != SLIM_OK) return s;
-  if ((s = m->alloc(&o.pair_pt, (size_t)cap)) != SLIM_OK) return s;
-  const int64_t pieces = (cap + kPiece - 1) / kPiece;
-  if ((s = m->alloc(&o.part, (size_t)pieces * 2 * (size_t)m->L)) != SLIM_OK) return s;
-  if ((s = m->alloc(&o.meta, (size_t)pieces * 2)) != SLIM_OK) return s;
-  if ((s = m->alloc(&o.ctr, (size_t)kOpCounters)) != SLIM_OK) return s;
-  unsigned char* tmp = nullptr;
-  if ((s = m->alloc(&tmp, radix_sort_temp_bytes(cap))) != SLIM_OK) return s;
-  o.tmp = tmp;
+  if ((s = m->alloc(&o.acc.rows, rc * (uint64_t)o.acc.stride)) != SLIM_OK) return s;
+  if ((s = m->alloc(&o.acc.listed, rc)) != SLIM_OK) return s;
+  if ((s = m->alloc(&o.acc.list, rc)) != SLIM_OK) return s;
+  if ((s = m->alloc(&o.acc.count, (size_t)1)) != SLIM_OK) return s;
+  if (cudaMemset(o.acc.rows, 0, rc * (uint64_t)o.acc.stride * sizeof(float)) != cudaSuccess ||
+      cudaMemset(o.acc.listed, 0, rc * sizeof(uint32_t)) != cudaSuccess)
+    return fail(SLIM_ERR_CUDA, "cudaMemset of the open-set accumulators failed");
   return SLIM_OK;
 }
 
-cudaError_t open_setup_attributes(slim_map*) { return cudaSuccess; }
-
-static int ceil_log2(uint64_t x) {
-  int b = 0;
-  while ((1ull << b) < x) ++b;
-  return b;
+bool open_encode_sem(CUtensorMap* map, const float* sem, int64_t n, int L, int row_pts) {
+  auto fn = get_encode();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)L, (cuuint64_t)std::max<int64_t>(n, 1)};
+  cuuint64_t strides[1] = {(cuuint64_t)L * 4};
+  cuuint32_t box[2] = {(cuuint32_t)kOE, (cuuint32_t)row_pts};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(sem), dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
-slim_status open_integrate(slim_map* m, const MapView& mv, OpenScratch& o, const ScanGeom& g,
-                           const float* pts, const float* sem, int64_t n, int L, int bf16,
-                           cudaStream_t st) {
-  if (n <= 0) return SLIM_OK;
-  cudaError_t e = cudaMemsetAsync(o.ctr, 0, kOpCounters * sizeof(uint32_t), st);
-  if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
-  const unsigned grid = (unsigned)((n + 255) / 256);
-  int tok = prof_begin(m, SLIM_KERNEL_OPEN_PAIRS, st);
-  k_open_pairs<<<grid, 256, 0, st>>>(mv, g, pts, n, o.keys, o.vals, o.pair_d, o.pair_pt, o.ctr,
-                                     (uint32_t)o.pair_cap);
-  const int64_t n_max = std::min<int64_t>(o.pair_cap, n * (int64_t)g.cap);
-  // keys of pairs without a block (0xFFFFFFFF) must sort after every valid
-  // key within the sorted bits: valid keys stay below (block_cap + 1) << 9
-  const int bits = 9 + ceil_log2((uint64_t)mv.block_cap + 1);
-  uint32_t* skeys = nullptr;  // the sorted pairs: (keys, vals) or the ping-pong pair
-  uint32_t* svals = nullptr;
-  e = radix_sort_u32_devn(o.keys, o.vals, o.keys_tmp, o.vals_tmp, o.tmp, n_max, o.ctr + kOpPairs,
-                          bits, st, &skeys, &svals);
-  if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
-  prof_end(m, tok, st);
-  tok = prof_begin(m, SLIM_KERNEL_OPEN_APPLY, st);
-  const int64_t pieces = (n_max + kPiece - 1) / kPiece;
-  const unsigned fgrid = (unsigned)((pieces + 7) / 8);
-  const unsigned mgrid = 152 * 8;
-  if (bf16) {
-    k_open_frag<1><<<fgrid, 256, 0, st>>>(mv, skeys, svals, o.pair_d, o.pair_pt, o.ctr, sem, L,
-                                          n_max, o.part, o.meta);
-    k_open_merge<1><<<mgrid, 256, 0, st>>>(mv, o.ctr, L, n_max, o.part, o.meta);
-  } else {
-    k_open_frag<0><<<fgrid, 256, 0, st>>>(mv, skeys, svals, o.pair_d, o.pair_pt, o.ctr, sem, L,
-                                          n_max, o.part, o.meta);
-    k_open_merge<0><<<mgrid, 256, 0, st>>>(mv, o.ctr, L, n_max, o.part, o.meta);
+uint32_t open_job_tiles(OpenJob& J) {
+  if (J.n <= 0) return 0;
+  if (J.width > 0) {
+    const int tw = 1 << J.tw_log2, th = kOT / tw;
+    J.tiles_x = (uint32_t)((J.width + tw - 1) / tw);
+    const int64_t rows = (J.n + J.width - 1) / J.width;
+    return J.tiles_x * (uint32_t)((rows + th - 1) / th);
   }
-  prof_end(m, tok, st);
-  e = cudaGetLastError();
+  J.tiles_x = 0;
+  return (uint32_t)((J.n + kOT - 1) / kOT);
+}
+
+cudaError_t launch_open_tiles(OpenBatch& b, int bf16, cudaStream_t st) {
+  uint32_t total = 0;
+  for (int k = 0; k < b.n_jobs; ++k) {
+    b.job[k].tile_begin = total;
+    total += open_job_tiles(b.job[k]);
+  }
+  b.total_tiles = total;
+  if (total == 0) return cudaSuccess;
+  const size_t sm = open_tile_smem_bytes();
+  if (bf16)
+    k_open_tile<1><<<total, kOThreads, sm, st>>>(b);
+  else
+    k_open_tile<0><<<total, kOThreads, sm, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_open_apply(const OpenApplyBatch& a, int bf16, cudaStream_t st) {
+  if (a.n_jobs == 0) return cudaSuccess;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (bf16)
+    k_open_apply<1><<<(unsigned)(sms * 8), 256, 0, st>>>(a);
+  else
+    k_open_apply<0><<<(unsigned)(sms * 8), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace slim
+
+namespace slim {
+
+__global__ void __launch_bounds__(256) k_reset_vox_rows(int4* vox_row, const uint32_t* ctr,
+                                                        uint32_t block_cap) {
+  const uint32_t nb = min(*(volatile const uint32_t*)&ctr[kCtrBlocks], block_cap);
+  const size_t n4 = (size_t)nb * kBlockVoxels / 4;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (size_t)gridDim.x * blockDim.x)
+    vox_row[i] = make_int4(-1, -1, -1, -1);
+}
+
+cudaError_t launch_reset_vox_rows(const MapView& mv, cudaStream_t st) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_reset_vox_rows<<<(unsigned)(sms * 4), 256, 0, st>>>(reinterpret_cast<int4*>(mv.vox_row),
+                                                         mv.ctr, mv.block_cap);
+  return cudaGetLastError();
+}
+
+slim_status open_fill_job(slim_map* m, OpenJob& J, const ScanGeom& g, const float* pts,
+                          const float* sem, int64_t n, int width) {
+  J.mv = m->mv;
+  J.g = g;
+  J.acc = m->open.acc;
+  J.pts = pts;
+  J.sem = sem;
+  J.n = n;
+  J.L = m->L;
+  J.width = width;
+  J.tw_log2 = m->open.tw_log2;
+  if (!open_encode_sem(&J.sem_map, sem, n, m->L, width > 0 ? 1 << J.tw_log2 : kORowPts))
+    return fail(SLIM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the embeddings");
+  return SLIM_OK;
+}
+
+slim_status open_integrate(slim_map* m, const ScanGeom& g, const float* pts, const float* sem,
+                           int64_t n, int width, cudaStream_t st) {
+  if (n <= 0) return SLIM_OK;
+  OpenBatch b;
+  b.n_jobs = 1;
+  slim_status s = open_fill_job(m, b.job[0], g, pts, sem, n, width);
+  if (s != SLIM_OK) return s;
+  cudaError_t e = cudaMemsetAsync(m->open.acc.count, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  int tok = prof_begin(m, SLIM_KERNEL_OPEN_TILE, st);
+  e = launch_open_tiles(b, m->bf16, st);
+  prof_end(m, tok, st);
+  if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  OpenApplyBatch a;
+  a.n_jobs = 1;
+  a.job[0].mv = m->mv;
+  a.job[0].acc = m->open.acc;
+  a.job[0].L = m->L;
+  tok = prof_begin(m, SLIM_KERNEL_OPEN_APPLY, st);
+  e = launch_open_apply(a, m->bf16, st);
+  prof_end(m, tok, st);
+  if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  return SLIM_OK;
+}
+
+// Open-set items of a batch: one tile launch per storage kind and 16 items,
+// then one apply launch per storage kind and 16 maps. Items of the same map
+// share the map's accumulators (one observation set).
+slim_status open_integrate_batch(const std::vector<OpenItem>& items, cudaStream_t st) {
+  if (items.empty()) return SLIM_OK;
+  std::vector<slim_map*> maps;
+  for (const OpenItem& it : items)
+    if (std::find(maps.begin(), maps.end(), it.map) == maps.end()) maps.push_back(it.map);
+  for (size_t k = 0; k < maps.size(); ++k) {
+    cudaError_t e = cudaMemsetAsync(maps[k]->open.acc.count, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  }
+  for (int bf = 0; bf < 2; ++bf) {
+    OpenBatch b;
+    b.n_jobs = 0;
+    slim_map* first = nullptr;
+    auto flush = [&]() -> slim_status {
+      if (b.n_jobs == 0) return SLIM_OK;
+      const int tok = prof_begin(first, SLIM_KERNEL_OPEN_TILE, st);
+      cudaError_t e = launch_open_tiles(b, bf, st);
+      prof_end(first, tok, st);
+      b.n_jobs = 0;
+      first = nullptr;
+      return e == cudaSuccess ? SLIM_OK : fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+    };
+    for (const OpenItem& it : items) {
+      if (it.map->bf16 != bf || it.n <= 0) continue;
+      if (!first) first = it.map;
+      slim_status s = open_fill_job(it.map, b.job[b.n_jobs], it.g, it.pts, it.sem, it.n,
+                                    it.width);
+      if (s != SLIM_OK) return s;
+      if (++b.n_jobs == kMaxOpenJobs) {
+        if ((s = flush()) != SLIM_OK) return s;
+      }
+    }
+    slim_status s = flush();
+    if (s != SLIM_OK) return s;
+  }
+  for (int bf = 0; bf < 2; ++bf) {
+    OpenApplyBatch a;
+    a.n_jobs = 0;
+    slim_map* first = nullptr;
+    auto flush = [&]() -> slim_status {
+      if (a.n_jobs == 0) return SLIM_OK;
+      const int tok = prof_begin(first, SLIM_KERNEL_OPEN_APPLY, st);
+      cudaError_t e = launch_open_apply(a, bf, st);
+      prof_end(first, tok, st);
+      a.n_jobs = 0;
+      first = nullptr;
+      return e == cudaSuccess ? SLIM_OK : fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+    };
+    for (slim_map* m : maps) {
+      if (m->bf16 != bf) continue;
+      if (!first) first = m;
+      a.job[a.n_jobs].mv = m->mv;
+      a.job[a.n_jobs].acc = m->open.acc;
+      a.job[a.n_jobs].L = m->L;
+      if (++a.n_jobs == kMaxOpenJobs) {
+        slim_status s = flush();
+        if (s != SLIM_OK) return s;
+      }
+    }
+    slim_status s = flush();
+    if (s != SLIM_OK) return s;
+  }
   return SLIM_OK;
 }
 

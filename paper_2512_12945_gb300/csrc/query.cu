@@ -31,6 +31,7 @@
 #include <mutex>
 
 #include "map.h"
+#include "tma.cuh"
 
 namespace slim {
 
@@ -38,7 +39,6 @@ constexpr int kQM = 128;        // voxel rows per tile
 constexpr int kQK = 64;         // K elements per stage (128-byte rows)
 constexpr int kQStages = 4;
 constexpr int kQThreads = 384;  // 12 warps: TMA, MMA, 8 epilogue, 2 row norms
-constexpr uint64_t kWaitNs = 500ull * 1000 * 1000;  // a wait gives up after 0.5 s
 
 struct QueryArgs {
   uint32_t n_rows;
@@ -57,54 +57,6 @@ struct QueryArgs {
   float* scores;        // [n_rows x Q] cosines or null
   uint32_t* status;     // map counters (sticky status)
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: false when kWaitNs of wall time ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 0;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 15) == 0 && global_ns() - t0 > kWaitNs) return false;
-    if (it > 64) __nanosleep(64);
-  }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x,
-                                            int32_t y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
 
 // K-major operand, 128-byte swizzle: rows of 128 B, 8-row atoms 1024 B apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -612,19 +564,6 @@ __global__ void k_rows_to_bf16(const float* __restrict__ in, __nv_bfloat16* out,
   if (lane == 0) norm2[row] = s;
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    cudaDriverEntryPointQueryResult q;
-    void* p = nullptr;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 static bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows,
                       uint32_t box_inner, uint32_t box_rows) {
   auto fn = get_encode();
@@ -708,14 +647,15 @@ slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float tempe
 // budget is fixed up front, or host programs that only hand in buffers they
 // already own. slim_query_rows_static serves them: its working memory is the
 // file-scope array below, which exists on every GPU that loads this library
-// for as long as the process lives. It holds the inverse query norms and a
-// status word (the row norms are computed inside k_query from the A tiles);
-// the region sized for the norms of kStaticQueryRows rows is kept as the
-// per-call row limit.
+// for as long as the process lives. It holds the inverse norms of at most
+// kStaticQueries queries and the status words of the call (the row norms are
+// computed inside k_query from the A tiles, so no per-row storage is needed).
+// kStaticQueryRows is a per-call maximum of the interface, not a size of the
+// array.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kStaticQueryRows = 1u << 20;  // rows per call (4 MiB of row norms)
+constexpr uint32_t kStaticQueryRows = 1u << 20;  // rows per call
 constexpr uint32_t kStaticQueries = 256;
-constexpr size_t kStaticWords = kStaticQueries + kStaticQueryRows + 64;
+constexpr size_t kStaticWords = kStaticQueries + kNumCounters;
 static __device__ __align__(256) float g_static_query_scratch[kStaticWords];
 
 namespace {
@@ -771,9 +711,8 @@ extern "C" slim_status slim_query_rows_static(const uint16_t* rows_dev, int64_t 
   if (n_rows == 0) return SLIM_OK;
   cudaStream_t st = (cudaStream_t)stream;
   float* qinv = scratch;
-  float* rnorm2 = scratch + kStaticQueries;
-  uint32_t* status = reinterpret_cast<uint32_t*>(scratch + kStaticQueries + kStaticQueryRows);
-  // the status word must start at zero; the norms are overwritten below
+  uint32_t* status = reinterpret_cast<uint32_t*>(scratch + kStaticQueries);
+  // the status words must start at zero; the norms are overwritten below
   e = cudaMemsetAsync(status, 0, kNumCounters * sizeof(uint32_t), st);
   if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
   const uint32_t rows = (uint32_t)n_rows;
@@ -809,5 +748,15 @@ extern "C" slim_status slim_query_rows_static(const uint16_t* rows_dev, int64_t 
   k_query<<<grid, kQThreads, query_smem_bytes(N), st>>>(tA, tB, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  // a bounded wait inside k_query that ran out leaves its code in the status
+  // word: read it back (into pageable host memory: nothing to allocate)
+  uint32_t code = 0;
+  e = cudaMemcpyAsync(&code, status + kCtrStatus, sizeof(code), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
+  if (code != 0)
+    return fail((slim_status)code, code == kDevTimeout
+                                       ? "a bounded wait in the query kernel ran out"
+                                       : "the query kernel raised a device fault");
   return SLIM_OK;
 }

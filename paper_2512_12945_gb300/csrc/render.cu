@@ -125,17 +125,8 @@ __global__ void __launch_bounds__(256) k_render(const __grid_constant__ RenderAr
         }
       } else {
         const float* r = mv.rec + vox * mv.rs;
-        float S = 0.f;
-        if (mv.split) {
-          for (int c = 0; c < mv.K; ++c) {
-            S += r[2 * c];
-            W += r[2 * c + 1];
-          }
-        } else {
-          S = r[0];
-          W = r[1];
-        }
-        D = W > 0.f ? S / W : 0.f;
+        W = rec_weight(r, mv.K, mv.layout);
+        D = rec_sdf(r, mv.K, mv.layout);
       }
     }
     if (W > 0.f) {
@@ -160,15 +151,23 @@ __global__ void __launch_bounds__(256) k_render(const __grid_constant__ RenderAr
         } else if (!a.open) {
           const size_t vox = (size_t)slot * kBlockVoxels + local_index(ry.i0, ry.i1, ry.i2);
           const float* r = mv.rec + vox * mv.rs;
-          const float* cnt = mv.split ? r + 1 : r + kSoftCnt;
-          const int cs = mv.split ? 2 : 1;
           lab = 0;
-          float bv = cnt[0];
-          for (int c = 1; c < mv.K; ++c)
-            if (cnt[c * cs] > bv) {
-              bv = cnt[c * cs];
-              lab = c;
-            }
+          if (mv.layout == kRecSoftFx) {  // exact integer counts
+            const long long* q = rec_fx(r) + 2;
+            long long bv = q[0];
+            for (int c = 1; c < mv.K; ++c)
+              if (q[c] > bv) {
+                bv = q[c];
+                lab = c;
+              }
+          } else {
+            float bv = r[1];
+            for (int c = 1; c < mv.K; ++c)
+              if (r[2 * c + 1] > bv) {
+                bv = r[2 * c + 1];
+                lab = c;
+              }
+          }
         }
         if (a.label) a.label[pix] = lab;
         if (a.sim) {

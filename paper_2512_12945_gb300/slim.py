@@ -45,7 +45,8 @@ class slim_map_params(ctypes.Structure):
                 ("block_capacity", ctypes.c_int64), ("hash_capacity", ctypes.c_int64),
                 ("voxel_capacity", ctypes.c_int64), ("max_points", ctypes.c_int64),
                 ("aggregation", ctypes.c_int32), ("tile_points", ctypes.c_int32),
-                ("weighting", ctypes.c_int32), ("weight_eps", ctypes.c_float)]
+                ("weighting", ctypes.c_int32), ("weight_eps", ctypes.c_float),
+                ("image_width", ctypes.c_int32)]
 
 
 class slim_stats(ctypes.Structure):
@@ -64,7 +65,7 @@ EXPORTS = ["slim_map_params_default", "slim_map_create", "slim_map_destroy", "sl
            "slim_extract_tsdf", "slim_query", "slim_backward", "slim_integrate_batch",
            "slim_profile_enable", "slim_profile_read", "slim_autotune", "slim_query_rows_static",
            "slim_extract_uncertainty", "slim_render", "slim_integrate_depth", "slim_last_error"]
-KERNELS = ["traverse", "fuse_closed", "open_pairs", "open_apply", "query", "backward", "batch",
+KERNELS = ["traverse", "fuse_closed", "open_tile", "open_apply", "query", "backward", "batch",
            "reset", "render"]
 N_KINDS = 16
 
@@ -373,7 +374,7 @@ class Map:
                  embed_storage="f32", min_range=0.0, max_range=1e30, alpha0=1.0,
                  body_from_sensor=None, block_capacity=100000, hash_capacity=262144,
                  voxel_capacity=1000000, max_points=1 << 18, aggregation="auto",
-                 tile_points=0, weighting="constant", weight_eps=0.0):
+                 tile_points=0, weighting="constant", weight_eps=0.0, image_width=0):
         p = slim_map_params_default()
         p.voxel_size = voxel_size
         p.trunc = trunc
@@ -396,6 +397,7 @@ class Map:
         p.tile_points = tile_points
         p.weighting = WEIGHTING[weighting] if isinstance(weighting, str) else int(weighting)
         p.weight_eps = weight_eps
+        p.image_width = image_width
         self.params = p
         self.mode = p.mode
         self.width = embed_dim if p.mode == SLIM_OPEN else num_classes

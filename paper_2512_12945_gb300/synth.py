@@ -262,6 +262,7 @@ class Workload:
     embed_dim: int
     body_from_sensor: np.ndarray
     scans: list              # list of dict(pts, pose, sem, labels)
+    image_width: int = 0     # organized frames: pixels per image row (0: unorganized)
 
     @property
     def n_points(self):
@@ -349,7 +350,29 @@ def indoor_rgbd(seed=3, n_frames=200, width=640, height=480, focal=525.0, dim=51
         sem = embeddings(frng, obj, cents, sigma)
         scans.append(dict(pts=pts, pose=pose, sem=sem, labels=obj))
     return Workload("indoor-rgbd", voxel, 3.0 * voxel, 0.3, 8.0, "open", 0, dim, np.eye(4),
-                    scans)
+                    scans, image_width=width)
+
+
+def indoor_centroids(seed=3, dim=512, n_objects=30):
+    """The class centroids indoor_rgbd draws for `seed` (after its scene)."""
+    rng = np.random.default_rng(seed)
+    sc = indoor_scene(rng, n_objects=n_objects)
+    return unit_centroids(rng, sc.n_objects(), dim)
+
+
+def indoor_embeddings_device(labels, centroids, seed, frame, sigma=0.1):
+    """Device-side draw of the indoor embeddings for long runs:
+    z = normalize(centroid[label] + N(0, sigma^2 I)) per pixel, float32, on
+    the device of `labels` (a torch int64 tensor) from a torch generator
+    seeded by (seed, frame). Same distribution as `embeddings`, not the same
+    numbers."""
+    import torch
+    dev = labels.device
+    g = torch.Generator(device=dev).manual_seed(int(seed) * 100003 + int(frame))
+    c = torch.as_tensor(centroids, dtype=torch.float32, device=dev)
+    z = c[labels] + sigma * torch.randn((labels.shape[0], c.shape[1]), device=dev, generator=g)
+    z /= torch.linalg.vector_norm(z, dim=1, keepdim=True)
+    return z.contiguous()
 
 
 def random_queries(seed, n, dim):

@@ -29,6 +29,8 @@ def gpu_map(w, mode=None, scans=None, **kw):
                 embed_dim=w.embed_dim if w.embed_dim else 64, min_range=w.min_range,
                 max_range=w.max_range, body_from_sensor=w.body_from_sensor,
                 max_points=max(s["pts"].shape[0] for s in w.scans))
+    if mode == "open":
+        args["image_width"] = getattr(w, "image_width", 0)
     args.update(kw)
     m = slim.Map(**args)
     for s in (w.scans if scans is None else scans):

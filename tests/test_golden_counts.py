@@ -56,6 +56,13 @@ def test_adjoint_pair_counts_are_the_oracles():
         assert (g["points"], g["valid"], g["pairs"]) == (s["points"], s["valid"], s["pairs"])
 
 
+def test_indoor_counts_first_frames_are_the_oracles():
+    stored = _load("indoor_rgbd_counts.json")
+    assert stored["meta"]["frames"] == len(stored["scans"]) == 200
+    w = synth.indoor_rgbd(seed=3, n_frames=200, width=640, height=480, dim=8, frames=[0, 1])
+    assert _rows(w, 2) == stored["scans"][:2]
+
+
 @pytest.mark.parametrize("name", ["street_lidar_counts.json", "room_lidar_counts.json",
                                   "indoor_rgbd_counts.json"])
 def test_stored_counts_are_consistent(name):

@@ -1,6 +1,7 @@
 """Batched integration: many maps of both kinds and uneven scan sizes in one
-slim_integrate_batch call (closed-set scans in one persistent launch), eager
-and captured in a CUDA graph, against per-map integration and the oracle."""
+slim_integrate_batch call, eager and captured in a CUDA graph, against
+per-map integration and against the oracle (every map, closed and open;
+the 16-map configuration of the benchmark at full size included)."""
 import numpy as np
 import pytest
 
@@ -60,6 +61,19 @@ def _compare_open(g, o):
         assert_close(g[k], o[k], 2.0 ** -7, 2.0 ** -9 * np.abs(o[k]).max(), k)
 
 
+def _compare_open_oracle(g, o, n_scans):
+    """BF16-stored means against the oracle's FP64 fusion: bit-exact key set
+    and weights, D within the parity tolerance, and m and beta within one
+    BF16 rounding per scan of the largest stored magnitude (half an ulp,
+    2^-9, for m; beta's update also reads the rounded m: 2^-8)."""
+    assert np.array_equal(g["ijk"], o["ijk"]), "voxel key sets differ"
+    assert np.array_equal(g["W"].astype(np.float64), o["W"]), "weights differ"
+    assert_close(g["D"], o["D"], RTOL, ATOL, "D")
+    for k, ulp in (("sem", 2.0 ** -9), ("beta", 2.0 ** -8)):
+        err = np.abs(g[k] - o[k])
+        assert err.max() <= n_scans * ulp * np.abs(o[k]).max() + 1e-6, (k, err.max())
+
+
 def test_batch_matches_per_map_and_oracle():
     from paper_2512_12945_gb300 import slim
     closed, opened = _workloads()
@@ -77,8 +91,38 @@ def test_batch_matches_per_map_and_oracle():
         g = to_np(m.extract())
         compare_closed(g, r, "onehot")
         compare_closed(g, oracle_map(w).extract(), "onehot")
-    for m, r in zip(maps[4:], refs[4:]):
-        _compare_open(to_np(m.extract()), r)
+    for m, r, w in zip(maps[4:], refs[4:], opened):
+        g = to_np(m.extract())
+        _compare_open(g, r)
+        _compare_open_oracle(g, oracle_map(w).extract(), len(w.scans))
+
+
+def test_batch_full_16_maps_vs_oracle():
+    """The benchmark's batched configuration at full size: 8 closed-set street
+    maps (64 beams, 320-3900 azimuths, 20 classes) and 8 open-set RGB-D maps
+    (l = 256, 320 x 240 to 640 x 480, BF16 storage), 10 scans each, all in
+    one slim_integrate_batch call; every map against the oracle."""
+    from paper_2512_12945_gb300 import slim
+    closed, opened = synth.batch_workload(seed=5, n_scans=10)
+    maps = []
+    for w in closed:
+        maps.append(slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=20,
+                             min_range=w.min_range, max_range=w.max_range,
+                             body_from_sensor=w.body_from_sensor,
+                             max_points=max(s["pts"].shape[0] for s in w.scans),
+                             block_capacity=200000, hash_capacity=1 << 19))
+    for w in opened:
+        maps.append(slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, mode="open",
+                             embed_dim=w.embed_dim, embed_storage="bf16",
+                             min_range=w.min_range, max_range=w.max_range,
+                             max_points=w.scans[0]["pts"].shape[0], voxel_capacity=400000,
+                             image_width=w.image_width))
+    items = _items(maps, closed + opened)
+    slim.slim_integrate_batch(items)
+    for m, w in zip(maps[:8], closed):
+        compare_closed(to_np(m.extract()), oracle_map(w).extract(), "onehot")
+    for m, w in zip(maps[8:], opened):
+        _compare_open_oracle(to_np(m.extract()), oracle_map(w).extract(), len(w.scans))
 
 
 def test_batch_in_cuda_graph():

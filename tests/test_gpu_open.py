@@ -92,11 +92,11 @@ def test_open_voxel_capacity_fault():
     assert e.value.status == 3
 
 
-def test_open_long_runs_split_across_pieces():
+def test_open_long_runs_many_tiles():
     """Full-resolution depth frames where single voxels collect thousands of
-    pixel observations in one frame (the camera close to a wall): runs far
-    longer than one piece of sorted pairs are cut and merged, and must give
-    the same batch update as the oracle's sequential one."""
+    pixel observations in one frame (the camera close to a wall), summed by
+    many tiles into one accumulator: the same update as the oracle's
+    sequential one."""
     w = synth.indoor_rgbd(seed=3, n_frames=200, width=640, height=480, dim=64,
                           frames=[100, 0, 50])
     g = to_np(gpu_map(w, voxel_capacity=400000).extract())
@@ -120,3 +120,83 @@ def test_open_max_dim_1024_bf16():
     for k, ulp in (("sem", 2.0 ** -9), ("beta", 2.0 ** -8)):
         err = np.abs(g[k] - o[k])
         assert err.max() <= n * ulp * np.abs(o[k]).max() + 1e-6, k
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_open_full_frames_640x480_dim512(storage):
+    """The indoor benchmark's frames at full size: 640 x 480 pixels, l = 512,
+    both storages, against the oracle (FP32: the parity tolerance; BF16: one
+    storage rounding per scan, as in test_open_bf16_storage_error_bound)."""
+    w = synth.indoor_rgbd(seed=3, n_frames=200, width=640, height=480, dim=512,
+                          frames=[0, 7])
+    g = to_np(gpu_map(w, embed_storage=storage, voxel_capacity=400000).extract())
+    o = oracle_map(w).extract()
+    if storage == "f32":
+        _compare(g, o)
+        return
+    assert np.array_equal(g["ijk"], o["ijk"])
+    assert np.array_equal(g["W"].astype(np.float64), o["W"])
+    assert_close(g["D"], o["D"], RTOL, ATOL, "D")
+    n = len(w.scans)
+    for k, ulp in (("sem", 2.0 ** -9), ("beta", 2.0 ** -8)):
+        err = np.abs(g[k] - o[k])
+        assert err.max() <= n * ulp * np.abs(o[k]).max() + 1e-6, (k, err.max())
+
+
+def test_open_unorganized_points():
+    """The same frames passed as unorganized points (tiles of 256
+    consecutive points instead of 16 x 16 pixels): the tiling changes how
+    observations are grouped, not the result."""
+    w = _work(frames=3, w=160, h=120, dim=64)
+    g = to_np(gpu_map(w, voxel_capacity=200000, image_width=0).extract())
+    o = oracle_map(w).extract()
+    _compare(g, o)
+
+
+def test_open_tile_overflow_splits():
+    """Scattered points (random directions and ranges, wide band): 256
+    consecutive points touch thousands of distinct voxels, more than a
+    tile's tables hold, so every tile is split into smaller pixel ranges
+    until each fits; the result is unchanged."""
+    rng = np.random.default_rng(7)
+    n = 3000
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts = (d * rng.uniform(0.5, 3.0, (n, 1))).astype(np.float32)
+    z = rng.standard_normal((n, 64))
+    z /= np.linalg.norm(z, axis=1, keepdims=True)
+    w = _work(frames=1)
+    w.trunc = 4 * w.voxel_size  # the widest band: 27 voxels per point
+    w.image_width = 0
+    w.scans = [dict(pts=pts, pose=np.eye(4), sem=z.astype(np.float32)),
+               dict(pts=pts[::-1].copy(), pose=np.eye(4), sem=z[::-1].astype(np.float32).copy())]
+    g = to_np(gpu_map(w, voxel_capacity=400000, block_capacity=100000).extract())
+    o = oracle_map(w).extract()
+    _compare(g, o)
+
+
+@pytest.mark.parametrize("tile_w", [8, 32])
+def test_open_tile_shapes(tile_w):
+    """Tiles of 8 x 32 and 32 x 8 pixels (the autotuner's other candidates):
+    same result as the oracle."""
+    w = _work(frames=3, w=160, h=120, dim=64)
+    g = to_np(gpu_map(w, voxel_capacity=200000, tile_points=tile_w).extract())
+    o = oracle_map(w).extract()
+    _compare(g, o)
+
+
+def test_open_autotune_picks_a_tile_shape():
+    from paper_2512_12945_gb300 import slim
+    w = _work(frames=2, w=320, h=240, dim=128)
+    m = gpu_map(w, scans=[], voxel_capacity=200000)
+    s = w.scans[0]
+    best = m.autotune(torch.from_numpy(s["pts"]).cuda(), s["pose"],
+                      torch.from_numpy(s["sem"]).cuda())
+    assert best in (8, 16, 32)
+    assert m.stats()["voxels"] == 0  # the map is left empty
+    for s in w.scans:
+        m.integrate(torch.from_numpy(s["pts"]).cuda(), s["pose"], torch.from_numpy(s["sem"]).cuda())
+    _compare(to_np(m.extract()), oracle_map(w).extract())
+    u = gpu_map(w, scans=[], voxel_capacity=200000, image_width=0)
+    assert u.autotune(torch.from_numpy(s["pts"]).cuda(), s["pose"],
+                      torch.from_numpy(s["sem"]).cuda()) == 0

@@ -74,7 +74,9 @@ def _closed(case, w, mode, max_keys=0.0, max_w=0.0, **kw):
     if mode == "onehot":
         _report(case, "count err (integers)", float(np.round(dc).max()), 0.0)
     else:
-        _report(case, "soft count err / W^2 eps", float((dc / (W * W * EPS32 + 1e-30)).max()),
+        # exact fixed-point sums (unit 2^-32) rounded once to FP32; the counts
+        # recovered from the FP32 posterior carry its rounding times K + W
+        _report(case, "soft count err / (K+W) eps", float((dc / ((K * alpha0 + W) * EPS32)).max()),
                 8.0)
     dp = np.abs(g["sem"][ig] - o["sem"][io]).max()
     _report(case, "posterior abs err", float(dp), 1e-5)
