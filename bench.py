@@ -4,18 +4,23 @@
 Workload: the urban LiDAR sequence — 100 scans of 64 beams x 2048 azimuths
 (131,072 points per scan, ~120k valid, ranges 1-80 m) ray-cast in a seeded
 synthetic street, 0.1 m voxels, 0.3 m truncation, 20 classes (closed-set
-one-hot Dirichlet counts). One step = empty the map and integrate all 100
-scans through the C ABI (slim_integrate per scan) with inputs resident in
-HBM (1.2 GB per step, larger than L2, so every step streams from HBM).
+one-hot Dirichlet counts). One step = empty the map (slim_map_reset) and
+integrate all 100 scans with one slim_integrate_batch call (16 scans per
+launch of the autotuned strategy) with inputs resident in HBM (1.2 GB per
+step, larger than L2, so every step streams from HBM).
 
 Prints one JSON line. Extra keys: roofline (dominant kernel, algorithmic
 bytes from the oracle's stored per-scan counts / CUDA-event kernel time in
-the timed region), e2e (slim_integrate_host from pinned host buffers, H2D
-copies and a D2H read of the map counters inside the timed region),
-cpu_baseline (the oracle on a bounded sample, host cores), clocks.
+the timed region), e2e (the same step from pinned host buffers with the
+host-to-device traffic and a D2H read of the map counters inside the timed
+region: slim_integrate_host per scan, and the batched call reading the
+pinned arrays in place; the faster is reported), cpu_baseline (the oracle on
+a bounded sample, host cores), variants (per-scan calls, other strategies),
+clocks.
 
 --impl reference times the oracle (plain sequential CPU restatement) on
-this host, one full scan per step.
+this host; --workload selects the secondary lines (room, indoor, adjoint,
+batch, render).
 """
 from __future__ import annotations
 
@@ -426,88 +431,81 @@ def run_ours(args):
     e2e = None
     n_e2e = args.e2e_steps or min(args.steps, 10)
     # the scans stacked in pinned host memory (every scan has the same number
-    # of points), so a chunk of scans is one contiguous host -> device copy
-    # per array
+    # of points)
     npts = max(s["pts"].shape[0] for s in w.scans)
     assert all(s["pts"].shape[0] == npts for s in w.scans)
-    K = w.num_classes
     pts_h = torch.from_numpy(np.stack([s["pts"] for s in w.scans])).pin_memory()
     sem_h = torch.from_numpy(np.stack([s["sem"] for s in w.scans])).pin_memory()
     st_c = slim.slim_stats()
     h2d = pts_h.numel() * 4 + sem_h.numel() * 4
 
-    # a user-level pipeline over the public API: chunks of 16 scans are
-    # copied host -> device on two copy streams (each half of the chunk's
-    # bytes, so two copy engines run) into two staging buffers while
-    # slim_integrate_batch integrates the previous chunk on the main stream
-    CH = 16
-    stage_p = [torch.empty((CH, npts, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
-    stage_s = [torch.empty((CH, npts, K), dtype=torch.float32, device="cuda") for _ in range(2)]
-    chunks = [list(range(i, min(i + CH, len(w.scans)))) for i in range(0, len(w.scans), CH)]
-    citems = []
-    for ci, ch in enumerate(chunks):
-        b = ci % 2
-        arr = (slim.slim_batch_item * len(ch))()
-        for k, sidx in enumerate(ch):
-            arr[k].map = h
-            arr[k].pts_dev = stage_p[b][k].data_ptr()
-            arr[k].n = npts
-            for q in range(16):
-                arr[k].pose[q] = float(poses[sidx][q])
-            arr[k].sem_dev = stage_s[b][k].data_ptr()
-        citems.append(arr)
-    copy_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    # (a) slim_integrate_host per scan: the library copies each scan into one
+    # of its two staging buffers on its own copy stream while the previous
+    # scan integrates; (b) the same batched call as the device-resident step,
+    # its items pointing at the pinned host arrays, which the kernels read in
+    # place over the host link (no staging copy)
+    zitems = (slim.slim_batch_item * len(w.scans))()
+    for k in range(len(w.scans)):
+        zitems[k].map = h
+        zitems[k].pts_dev = pts_h[k].data_ptr()
+        zitems[k].n = npts
+        for q in range(16):
+            zitems[k].pose[q] = float(poses[k][q])
+        zitems[k].sem_dev = sem_h[k].data_ptr()
+    hargs = [(ctypes.c_void_p(pts_h[k].data_ptr()), npts, args_c[k][2],
+              ctypes.c_void_p(sem_h[k].data_ptr())) for k in range(len(w.scans))]
 
-    def step_host(start_ev=None):
+    def step_host():
         L.slim_map_reset(h, sp)
-        used = [None, None]
-        for ci, ch in enumerate(chunks):
-            b = ci % 2
-            lo, n_ch = ch[0], len(ch)
-            half = (n_ch + 1) // 2
-            for si, cs in enumerate(copy_streams):
-                a0, a1 = (0, half) if si == 0 else (half, n_ch)
-                if a1 <= a0:
-                    continue
-                with torch.cuda.stream(cs):
-                    if start_ev is not None and ci == 0:
-                        cs.wait_event(start_ev)
-                    if used[b] is not None:
-                        cs.wait_event(used[b])
-                    stage_p[b][a0:a1].copy_(pts_h[lo + a0:lo + a1], non_blocking=True)
-                    stage_s[b][a0:a1].copy_(sem_h[lo + a0:lo + a1], non_blocking=True)
-                    copied = torch.cuda.Event()
-                    copied.record(cs)
-                stream.wait_event(copied)
-            rc = L.slim_integrate_batch(citems[ci], len(ch), sp)
+        for a in hargs:
+            rc = L.slim_integrate_host(h, a[0], a[1], a[2], a[3], sp)
             if rc:
                 raise slim.SlimError(rc, L.slim_last_error().decode())
-            used[b] = torch.cuda.Event()
-            used[b].record(stream)
         rc = L.slim_map_stats(h, ctypes.byref(st_c), sp)  # D2H of the map counters
         if rc:
             raise slim.SlimError(rc, L.slim_last_error().decode())
 
-    step_host()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(n_e2e):
-        step_host(e0)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    e_ms = max(e0.elapsed_time(e1), wall * 1e3)
-    e_ms = max_over_ranks(e_ms, dist)
-    e2e = {"value": replica_rate(ws, valid_per_step * n_e2e, e_ms), "unit": UNIT,
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * 4, "steps": n_e2e,
-           "call": "pinned host -> device copies of 16-scan chunks (one per array and half "
-                   "chunk, on two copy streams), overlapped with slim_integrate_batch of the "
-                   "previous chunk, + slim_map_stats"}
+    def step_zero_copy():
+        L.slim_map_reset(h, sp)
+        rc = L.slim_integrate_batch(zitems, len(w.scans), sp)
+        if rc:
+            raise slim.SlimError(rc, L.slim_last_error().decode())
+        rc = L.slim_map_stats(h, ctypes.byref(st_c), sp)
+        if rc:
+            raise slim.SlimError(rc, L.slim_last_error().decode())
+
+    def time_e2e(fn):
+        fn()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        return max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3), dist)
+
+    e2e_var = {}
+    for name, fn, call in (
+            ("host_copy", step_host,
+             "slim_map_reset + slim_integrate_host per scan (the library's double-buffered "
+             "H2D copies on its copy stream, overlapped with the previous scan's integration) "
+             "+ slim_map_stats"),
+            ("zero_copy", step_zero_copy,
+             "slim_map_reset + slim_integrate_batch on the pinned host arrays (the kernels "
+             "read points and probabilities in place over the host link) + slim_map_stats")):
+        e_ms = time_e2e(fn)
+        e2e_var[name] = {"value": replica_rate(ws, valid_per_step * n_e2e, e_ms), "unit": UNIT,
+                         "ms_per_step": e_ms / n_e2e, "call": call}
+    best = max(e2e_var, key=lambda k: e2e_var[k]["value"])
+    e2e = {"value": e2e_var[best]["value"], "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": 8 * 4, "steps": n_e2e, "call": e2e_var[best]["call"],
+           "variants": e2e_var}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -9,10 +9,12 @@
  * and diagonal beta of an l-dimensional embedding (open set, Sec. III-D).
  *
  * Conventions for every entry point:
- *   - Pointers named *_dev are CUDA device memory owned by the caller; the
- *     library never frees them and never keeps them after the call returns
- *     (work it queued on `stream` may still read them until the stream
- *     reaches that point). Pointers named *_host are ordinary host memory.
+ *   - Pointers named *_dev are memory the GPU can address, owned by the
+ *     caller: device memory, or pinned (page-locked) host memory, which the
+ *     kernels then read in place over the host link. The library never frees
+ *     them and never keeps them after the call returns (work it queued on
+ *     `stream` may still read them until the stream reaches that point).
+ *     Pointers named *_host are ordinary host memory.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *     stream). Work is queued asynchronously on it unless stated otherwise.
  *   - Arguments are checked on the host before anything is queued; a bad
@@ -198,10 +200,14 @@ slim_status slim_integrate_depth(slim_map* m, const float* depth_dev, int32_t wi
                                  int32_t height, float fx, float fy, float cx, float cy,
                                  const double pose_host[16], const void* sem_dev, void* stream);
 
-/* As slim_integrate with pts_host / sem_host in host memory: the library
- * copies them into its own device staging buffers on `stream` (pinned host
- * memory makes the copies asynchronous). The host buffers must stay valid
- * until the stream reaches the copies. */
+/* As slim_integrate with pts_host / sem_host in host memory. The map keeps
+ * two device staging buffers and its own copy stream: the call copies the
+ * scan into the buffer the call before last used (once the integration that
+ * read it has run), makes `stream` wait for the copies and queues the
+ * integration there. Consecutive calls therefore overlap the copy of scan
+ * k + 1 with the integration of scan k. Pinned host memory makes the copies
+ * asynchronous; the host buffers must stay valid until the integration
+ * queued on `stream` has run. */
 slim_status slim_integrate_host(slim_map* m, const float* pts_host, int64_t n,
                                 const double pose_host[16], const void* sem_host,
                                 void* stream);

@@ -294,8 +294,15 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
     m->open.tw_log2 = p->tile_points == 8 ? 3 : (p->tile_points == 32 ? 5 : 4);
   }
   const int64_t mp = std::max<int64_t>(p->max_points, 1);
-  if ((s = m->alloc(&m->stage_pts, (size_t)mp * 3)) != SLIM_OK) return bail(s);
-  if ((s = m->alloc(&m->stage_sem, (size_t)mp * sem_width(m))) != SLIM_OK) return bail(s);
+  for (int k = 0; k < 2; ++k) {
+    if ((s = m->alloc(&m->stage_pts[k], (size_t)mp * 3)) != SLIM_OK) return bail(s);
+    if ((s = m->alloc(&m->stage_sem[k], (size_t)mp * sem_width(m))) != SLIM_OK) return bail(s);
+    if (cudaEventCreateWithFlags(&m->stage_copied[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->stage_free[k], cudaEventDisableTiming) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+  }
+  if (cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "cudaStreamCreate"));
   if ((s = m->alloc(&m->ex_keys, bc)) != SLIM_OK) return bail(s);
   if ((s = m->alloc(&m->ex_keys_tmp, bc)) != SLIM_OK) return bail(s);
   if ((s = m->alloc(&m->ex_slots, bc)) != SLIM_OK) return bail(s);
@@ -449,14 +456,24 @@ slim_status slim_integrate_host(slim_map* m, const float* pts_host, int64_t n,
   if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
   if (n < 0 || n > m->p.max_points) return fail(SLIM_ERR_ARG, "n must be in [0, max_points]");
   if (n > 0 && (!pts_host || !sem_host)) return fail(SLIM_ERR_ARG, "pts/sem NULL with n > 0");
+  if (!pose_host || !finite_pose(pose_host)) return fail(SLIM_ERR_ARG, "pose missing or not finite");
   cudaStream_t st = (cudaStream_t)stream;
-  if (n > 0) {
-    SLIM_CUDA(cudaMemcpyAsync(m->stage_pts, pts_host, (size_t)n * 3 * sizeof(float),
-                              cudaMemcpyHostToDevice, st));
-    SLIM_CUDA(cudaMemcpyAsync(m->stage_sem, sem_host, (size_t)n * sem_width(m) * sizeof(float),
-                              cudaMemcpyHostToDevice, st));
-  }
-  return slim_integrate(m, m->stage_pts, n, pose_host, m->stage_sem, stream);
+  if (n == 0) return slim_integrate(m, nullptr, 0, pose_host, nullptr, stream);
+  // staging buffer b is free once the integration that last read it (two
+  // calls ago) has run; its copies go on the map's copy stream, so they
+  // overlap the previous call's integration on `stream`
+  const int b = m->stage_next;
+  m->stage_next ^= 1;
+  SLIM_CUDA(cudaStreamWaitEvent(m->copy_stream, m->stage_free[b], 0));
+  SLIM_CUDA(cudaMemcpyAsync(m->stage_pts[b], pts_host, (size_t)n * 3 * sizeof(float),
+                            cudaMemcpyHostToDevice, m->copy_stream));
+  SLIM_CUDA(cudaMemcpyAsync(m->stage_sem[b], sem_host, (size_t)n * sem_width(m) * sizeof(float),
+                            cudaMemcpyHostToDevice, m->copy_stream));
+  SLIM_CUDA(cudaEventRecord(m->stage_copied[b], m->copy_stream));
+  SLIM_CUDA(cudaStreamWaitEvent(st, m->stage_copied[b], 0));
+  const slim_status s = slim_integrate(m, m->stage_pts[b], n, pose_host, m->stage_sem[b], stream);
+  SLIM_CUDA(cudaEventRecord(m->stage_free[b], st));
+  return s;
 }
 
 // Open-set maps of organized frames: time the tile shapes 8 x 32, 16 x 16

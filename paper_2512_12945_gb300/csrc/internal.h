@@ -55,15 +55,17 @@ int max_band_blocks();
 // open.cu: open-set integration by tiles of pixels aggregated on chip.
 // Per-row accumulators of one integration call of a map:
 //   rows[row * stride]: {sum d (int64, unit 2^-32 m), n (u32), pad,
-//                        (S1, S2) for each of the L elements}
+//                        (S1, S2) for each of the L elements (high halves),
+//                        the same (low halves: rounding errors of the
+//                        additions into the high halves)}
 struct OpenAcc {
   float* rows;      // [row_cap * stride], zero between calls
   uint32_t* listed; // [row_cap] 1 while the row is in list (cleared by the update)
   uint32_t* list;   // [row_cap] rows touched by the current call
   uint32_t* count;  // entries in list
-  int32_t stride;   // floats per accumulator row: 4 + 2 L
+  int32_t stride;   // floats per accumulator row: 4 + 4 L
 };
-struct alignas(64) OpenJob {
+struct OpenJob {  // 64-byte aligned by its tensor map
   CUtensorMap sem_map;  // the scan's embeddings as an L x n FP32 tensor
   MapView mv;
   ScanGeom g;

@@ -36,8 +36,14 @@ struct slim_map {
   slim::MapView mv{};
   std::vector<void*> allocs;
   size_t bytes = 0;
-  float* stage_pts = nullptr;
-  float* stage_sem = nullptr;
+  // slim_integrate_host: two device staging buffers, filled on the map's own
+  // copy stream while the previous call's integration runs
+  float* stage_pts[2] = {nullptr, nullptr};
+  float* stage_sem[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t stage_copied[2] = {nullptr, nullptr};
+  cudaEvent_t stage_free[2] = {nullptr, nullptr};
+  int stage_next = 0;
   // extract scratch
   uint64_t* ex_keys = nullptr;
   uint64_t* ex_keys_tmp = nullptr;
@@ -78,6 +84,13 @@ struct slim_map {
   void release() {
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     prof_ev.clear();
+    for (int k = 0; k < 2; ++k) {
+      if (stage_copied[k]) cudaEventDestroy(stage_copied[k]);
+      if (stage_free[k]) cudaEventDestroy(stage_free[k]);
+      stage_copied[k] = stage_free[k] = nullptr;
+    }
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    copy_stream = nullptr;
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
     if (pinned) cudaFreeHost(pinned);

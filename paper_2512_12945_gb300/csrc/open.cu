@@ -89,6 +89,33 @@ __device__ __forceinline__ void red_add_v4_nc(float* r, float a, float b, float 
                : "memory");
 }
 
+// old = *r; *r += (a, b, c, d), returning old (16-byte aligned).
+__device__ __forceinline__ float4 atom_add_v4(float* r, float a, float b, float c, float d) {
+  float4 o;
+  asm volatile("atom.global.add.v4.f32 {%0, %1, %2, %3}, [%4], {%5, %6, %7, %8};"
+               : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
+               : "l"(r), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+  return o;
+}
+
+// Rounding error of the addition old + x (Knuth's TwoSum with every
+// operation rounded on its own): (old + x) - fl(old + x), exactly.
+__device__ __forceinline__ float two_sum_err(float old, float x) {
+  const float t = __fadd_rn(old, x);
+  const float z = __fsub_rn(t, old);
+  return __fadd_rn(__fsub_rn(old, __fsub_rn(t, z)), __fsub_rn(x, z));
+}
+
+// Compensated (Kahan) step of a packed pair of sums: sum += y with the
+// running compensation c (sum - c tracks the exact sum to one rounding).
+__device__ __forceinline__ void f2_kahan(uint64_t& sum, uint64_t& c, uint64_t y) {
+  const uint64_t yc = f2_sub(y, c);
+  const uint64_t t = f2_add(sum, yc);
+  c = f2_sub(f2_sub(t, sum), yc);
+  sum = t;
+}
+
 __device__ __forceinline__ void red_add_u32(uint32_t* a, uint32_t v) {
   asm volatile("red.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
 }
@@ -193,6 +220,7 @@ struct OpenTileSmem {
   uint16_t order[kOMaxTV];         // tile voxels by decreasing pixel count
   uint32_t scan[kOThreads / 32];
   uint32_t misc[2];                // 0 status, 1 table overflow
+  uint32_t work[16];               // per chunk: next tile voxel for a warp
   uint32_t rowmask;                // staged rows holding a valid pixel
   int32_t parts[2 * 16];           // pending pixel ranges
   unsigned long long bar;
@@ -333,6 +361,7 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
         ++off;
       }
     }
+    if (tid < 16) s.work[tid] = 0u;
     for (int v = tid; v < (int)ntv; v += kOThreads) {
       s.tv_n[v] = 0;
       s.tv_dq[v] = 0ull;
@@ -431,7 +460,9 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
       s.order[rank] = (uint16_t)tid;
     }
     __syncthreads();
-    // 5. per chunk: sums of y = z - s and y^2 over each voxel's pixels
+    // 5. per chunk: sums of y = z - s and y^2 over each voxel's pixels, in
+    //    two alternating chains, the sums of y compensated (Kahan); warps
+    //    take voxels (longest first) from a shared counter
     for (int c = 0; c < nch; ++c) {
       if (cur != c) {  // the stage is free (barrier at the end of the last chunk)
         if (tid == 0) issue_chunk(s, J, lt, c, policy);
@@ -449,13 +480,17 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
         inflight = false;
       }
       const int e0 = c * kOE + 2 * (int)lane;
-      for (int k = (int)warp; k < (int)ntv; k += kOThreads / 32) {
+      for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(&s.work[c], 1u);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (k >= ntv) break;
         const int v = s.order[k];
         const int32_t row = s.tv_row[v];
         if (row < 0) continue;
         const float2 sh = load2<BF16>(mv.mrow, (size_t)row * L + e0);
         const uint64_t s2 = f2_pack(sh.x, sh.y);
-        uint64_t a1 = 0, a2 = 0, b1 = 0, b2 = 0;
+        uint64_t a1 = 0, a2 = 0, b1 = 0, b2 = 0, ca = 0, cb = 0;
 #pragma unroll 1
         for (int w = 0; w < kOT / 32; ++w) {
           uint32_t mk = s.tv_mask[v][w];
@@ -464,7 +499,7 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
             mk &= mk - 1;
             const uint64_t za = *reinterpret_cast<const uint64_t*>(&s.stage[pa * kOE + 2 * lane]);
             const uint64_t ya = f2_sub(za, s2);
-            a1 = f2_add(a1, ya);
+            f2_kahan(a1, ca, ya);
             a2 = f2_fma(ya, ya, a2);
             if (mk) {
               const int pb = 32 * w + __ffs(mk) - 1;
@@ -472,14 +507,19 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
               const uint64_t zb =
                   *reinterpret_cast<const uint64_t*>(&s.stage[pb * kOE + 2 * lane]);
               const uint64_t yb = f2_sub(zb, s2);
-              b1 = f2_add(b1, yb);
+              f2_kahan(b1, cb, yb);
               b2 = f2_fma(yb, yb, b2);
             }
           }
         }
-        const float2 S1 = f2_unpack(f2_add(a1, b1)), S2 = f2_unpack(f2_add(a2, b2));
-        red_add_v4_nc(J.acc.rows + (size_t)row * J.acc.stride + 4 + 2 * e0, S1.x, S2.x, S1.y,
-                      S2.y);
+        const float2 S1 = f2_unpack(f2_add(f2_sub(a1, ca), f2_sub(b1, cb)));
+        const float2 S2 = f2_unpack(f2_add(a2, b2));
+        // across tiles, compensated: the high half of the accumulator takes
+        // the sums, the low half the exact rounding error of each addition
+        float* hi = J.acc.rows + (size_t)row * J.acc.stride + 4 + 2 * e0;
+        const float4 old = atom_add_v4(hi, S1.x, S2.x, S1.y, S2.y);
+        red_add_v4_nc(hi + 2 * L, two_sum_err(old.x, S1.x), two_sum_err(old.y, S2.x),
+                      two_sum_err(old.z, S1.y), two_sum_err(old.w, S2.y));
       }
       __syncthreads();  // the stage is free again
     }
@@ -526,9 +566,12 @@ __global__ void __launch_bounds__(256) k_open_apply(const __grid_constant__ Open
         const size_t rb = (size_t)row * L;
         float nrm = 0.f;
         for (int e = 4 * (int)lane; e < L; e += 128) {
-          float4* a4 = reinterpret_cast<float4*>(h + 4 + 2 * e);
-          const float4 p = a4[0], q = a4[1];  // (S1, S2) of elements e .. e + 3
-          const float s1[4] = {p.x, p.z, q.x, q.z}, s2[4] = {p.y, p.w, q.y, q.w};
+          float4* a4 = reinterpret_cast<float4*>(h + 4 + 2 * e);          // high halves
+          float4* c4 = reinterpret_cast<float4*>(h + 4 + 2 * L + 2 * e);  // low halves
+          const float4 p = a4[0], q = a4[1], pc = c4[0], qc = c4[1];
+          // (S1, S2) of elements e .. e + 3
+          const float s1[4] = {p.x + pc.x, p.z + pc.z, q.x + qc.x, q.z + qc.z};
+          const float s2[4] = {p.y + pc.y, p.w + pc.w, q.y + qc.y, q.w + qc.w};
           const float4 m4 = load4<BF16>(mv.mrow, rb + e);
           const float4 b4 = seen ? load4<BF16>(mv.brow, rb + e) : make_float4(0.f, 0.f, 0.f, 0.f);
           float mv4[4] = {m4.x, m4.y, m4.z, m4.w}, bv4[4] = {b4.x, b4.y, b4.z, b4.w};
@@ -542,8 +585,7 @@ __global__ void __launch_bounds__(256) k_open_apply(const __grid_constant__ Open
           store4<BF16>(mv.brow, rb + e, make_float4(bv4[0], bv4[1], bv4[2], bv4[3]));
           if (BF16) mo = load4<BF16>(mv.mrow, rb + e);  // norm of the stored values
           nrm += mo.x * mo.x + mo.y * mo.y + mo.z * mo.z + mo.w * mo.w;
-          a4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-          a4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+          a4[0] = a4[1] = c4[0] = c4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xFFFFFFFFu, nrm, off);
@@ -553,7 +595,7 @@ __global__ void __launch_bounds__(256) k_open_apply(const __grid_constant__ Open
           reinterpret_cast<float4*>(h)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       } else {
-        for (int e = 4 * (int)lane; e < 2 * L + 4; e += 128)
+        for (int e = 4 * (int)lane; e < 4 * L + 4; e += 128)
           *reinterpret_cast<float4*>(h + e) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
@@ -573,7 +615,7 @@ cudaError_t open_setup_attributes() {
 
 slim_status open_alloc_scratch(slim_map* m, OpenScratch& o) {
   const uint64_t rc = (uint64_t)m->p.voxel_capacity;
-  o.acc.stride = 4 + 2 * m->L;
+  o.acc.stride = 4 + 4 * m->L;
   slim_status s;
   if ((s = m->alloc(&o.acc.rows, rc * (uint64_t)o.acc.stride)) != SLIM_OK) return s;
   if ((s = m->alloc(&o.acc.listed, rc)) != SLIM_OK) return s;

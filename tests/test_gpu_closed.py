@@ -100,19 +100,24 @@ def test_block_capacity_fault_is_reported(agg):
     m.sync()  # reset clears the status
 
 
-def test_host_entry_point_matches_device():
-    w = synth.room_lidar(n_scans=2, n_beams=16, n_az=128)
+def test_host_entry_point_matches_device_and_oracle():
+    """slim_integrate_host from pinned host buffers, six calls in a row (the
+    two staging buffers are each reused while the other call's copies run):
+    the same map as the device entry point and the oracle."""
+    w = synth.room_lidar(n_scans=6, n_beams=16, n_az=256)
     from paper_2512_12945_gb300 import slim
     a = gpu_map(w)
     b = slim.Map(voxel_size=w.voxel_size, trunc=w.trunc, num_classes=10, min_range=w.min_range,
                  max_range=w.max_range, max_points=w.scans[0]["pts"].shape[0])
-    for s in w.scans:
-        b.integrate_host(torch.from_numpy(s["pts"]).pin_memory(), s["pose"],
-                         torch.from_numpy(s["sem"]).pin_memory())
+    host = [(torch.from_numpy(s["pts"]).pin_memory(), torch.from_numpy(s["sem"]).pin_memory())
+            for s in w.scans]
+    for (p, q), s in zip(host, w.scans):
+        b.integrate_host(p, s["pose"], q)
     b.sync()
     ga, gb = to_np(a.extract()), to_np(b.extract())
     assert np.array_equal(ga["ijk"], gb["ijk"]) and np.array_equal(ga["W"], gb["W"])
     assert_close(ga["D"], gb["D"], RTOL, ATOL, "D")
+    compare_closed(gb, oracle_map(w).extract(), "onehot")
 
 
 @pytest.mark.parametrize("agg", ["sort", "hash"])

@@ -200,3 +200,17 @@ def test_open_autotune_picks_a_tile_shape():
     u = gpu_map(w, scans=[], voxel_capacity=200000, image_width=0)
     assert u.autotune(torch.from_numpy(s["pts"]).cuda(), s["pose"],
                       torch.from_numpy(s["sem"]).cuda()) == 0
+
+
+def test_open_host_entry_point():
+    """slim_integrate_host for the open set (embeddings copied from pinned
+    host memory into the map's staging buffers): the oracle's map."""
+    from paper_2512_12945_gb300 import slim
+    w = _work(frames=4, w=96, h=72, dim=64)
+    m = gpu_map(w, scans=[], voxel_capacity=200000)
+    host = [(torch.from_numpy(s["pts"]).pin_memory(), torch.from_numpy(s["sem"]).pin_memory())
+            for s in w.scans]
+    for (p, q), s in zip(host, w.scans):
+        m.integrate_host(p, s["pose"], q)
+    m.sync()
+    _compare(to_np(m.extract()), oracle_map(w).extract())
