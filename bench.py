@@ -664,6 +664,7 @@ def run_indoor(args):
                      embed_storage=storage, min_range=0.3, max_range=8.0,
                      max_points=640 * 480, block_capacity=200000, hash_capacity=1 << 20,
                      voxel_capacity=args.voxel_capacity, image_width=640)
+        tile_w = m.autotune(pts[0], poses[0], sem[0])  # tile shape of the open-set kernel
 
         def step():
             m.reset()
@@ -709,6 +710,7 @@ def run_indoor(args):
                      "k_open_apply); kernels_frac: the same bytes over the two kernels' "
                      "event time alone"}
         out[storage] = {"points_per_s": valid / (ms / 1e3), "ms_per_step": ms,
+                        "autotuned_tile_width": tile_w,
                         "ms_per_frame": ms / nf, "voxels": rows, "integrate_roofline": roof,
                         "depth_front_end": {"ms_per_step": dms,
                                             "points_per_s": valid / (dms / 1e3),

@@ -214,6 +214,8 @@ struct OpenTileSmem {
   uint64_t tv_key[kOMaxTV];
   unsigned long long tv_dq[kOMaxTV];  // sum of d, fixed point 2^-32 m
   uint32_t tv_mask[kOMaxTV][kOT / 32];
+  uint32_t tv_off[kOMaxTV];        // start of the voxel's pixel list in plist
+  uint16_t plist[kOT * 27];        // per voxel: its pixels' stage offsets (floats / 2)
   uint32_t tv_n[kOMaxTV];
   int32_t tv_row[kOMaxTV];
   uint32_t tv_flag[kOMaxTV];       // 1: row created here, 2: wait for another CTA
@@ -459,6 +461,30 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
       }
       s.order[rank] = (uint16_t)tid;
     }
+    // the pixel lists: offsets of the voxels' lists (exclusive scan of the
+    // counts), then one warp per voxel expands its mask, 8 pixels per lane
+    {
+      uint32_t tot;
+      const uint32_t o = cta_exclusive_scan(tid < (int)ntv ? s.tv_n[tid] : 0u, s.scan, &tot);
+      if (tid < (int)ntv) s.tv_off[tid] = o;
+      __syncthreads();
+      for (int v = (int)warp; v < (int)ntv; v += kOThreads / 32) {
+        const uint32_t bits = (s.tv_mask[v][lane >> 2] >> (8 * (lane & 3))) & 0xFFu;
+        uint32_t x = (uint32_t)__popc(bits);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+          if ((int)lane >= off) x += y;
+        }
+        uint32_t at = s.tv_off[v] + x - (uint32_t)__popc(bits);
+        uint32_t b = bits;
+        while (b) {
+          const int p = 8 * (int)lane + __ffs(b) - 1;
+          b &= b - 1;
+          s.plist[at++] = (uint16_t)(p * (kOE / 2));
+        }
+      }
+    }
     __syncthreads();
     // 5. per chunk: sums of y = z - s and y^2 over each voxel's pixels, in
     //    two alternating chains, the sums of y compensated (Kahan); warps
@@ -491,26 +517,22 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
         const float2 sh = load2<BF16>(mv.mrow, (size_t)row * L + e0);
         const uint64_t s2 = f2_pack(sh.x, sh.y);
         uint64_t a1 = 0, a2 = 0, b1 = 0, b2 = 0, ca = 0, cb = 0;
-#pragma unroll 1
-        for (int w = 0; w < kOT / 32; ++w) {
-          uint32_t mk = s.tv_mask[v][w];
-          while (mk) {
-            const int pa = 32 * w + __ffs(mk) - 1;
-            mk &= mk - 1;
-            const uint64_t za = *reinterpret_cast<const uint64_t*>(&s.stage[pa * kOE + 2 * lane]);
-            const uint64_t ya = f2_sub(za, s2);
-            f2_kahan(a1, ca, ya);
-            a2 = f2_fma(ya, ya, a2);
-            if (mk) {
-              const int pb = 32 * w + __ffs(mk) - 1;
-              mk &= mk - 1;
-              const uint64_t zb =
-                  *reinterpret_cast<const uint64_t*>(&s.stage[pb * kOE + 2 * lane]);
-              const uint64_t yb = f2_sub(zb, s2);
-              f2_kahan(b1, cb, yb);
-              b2 = f2_fma(yb, yb, b2);
-            }
-          }
+        const uint64_t* st64 = reinterpret_cast<const uint64_t*>(s.stage) + lane;
+        const uint32_t pb0 = s.tv_off[v], pe = pb0 + s.tv_n[v];
+        uint32_t i = pb0;
+        for (; i + 1 < pe; i += 2) {
+          const uint64_t za = st64[s.plist[i]];
+          const uint64_t zb = st64[s.plist[i + 1]];
+          const uint64_t ya = f2_sub(za, s2), yb = f2_sub(zb, s2);
+          f2_kahan(a1, ca, ya);
+          a2 = f2_fma(ya, ya, a2);
+          f2_kahan(b1, cb, yb);
+          b2 = f2_fma(yb, yb, b2);
+        }
+        if (i < pe) {
+          const uint64_t ya = f2_sub(st64[s.plist[i]], s2);
+          f2_kahan(a1, ca, ya);
+          a2 = f2_fma(ya, ya, a2);
         }
         const float2 S1 = f2_unpack(f2_add(f2_sub(a1, ca), f2_sub(b1, cb)));
         const float2 S2 = f2_unpack(f2_add(a2, b2));
