@@ -79,13 +79,14 @@ typedef enum { SLIM_STORE_F32 = 0, SLIM_STORE_BF16 = 1 } slim_storage;
  *   SLIM_AGG_HASH    one-hot only: a CTA tile adds each pair at once into a
  *                    shared-memory table keyed by (voxel, class), then sends
  *                    one vector red.add per table entry;
- *   SLIM_AGG_DIRECT  closed set: no grouping on chip, vector red.adds per
- *                    pair resolved in L2 (one thread per point; soft counts
- *                    send their K-vector four classes per reduction);
+ *   SLIM_AGG_DIRECT  closed set: no grouping on chip, reductions per pair
+ *                    resolved in L2 (one thread per point; soft counts send
+ *                    2 + K 64-bit fixed-point reductions per pair);
  *   SLIM_AGG_AUTO    one-hot: direct, or hash when tile_points is set;
  *                    slim_autotune picks between direct and the hash tiles;
- *                    soft counts: direct (20 % faster than sort on dense
- *                    scans; sort sums each voxel's pairs on chip first). */
+ *                    soft counts: sort (each voxel's pairs of a tile summed
+ *                    on chip before its 2 + K 64-bit fixed-point reductions;
+ *                    direct sends them per pair). */
 typedef enum {
   SLIM_AGG_AUTO = 0,
   SLIM_AGG_SORT = 1,

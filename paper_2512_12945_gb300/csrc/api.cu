@@ -175,6 +175,7 @@ slim_status check_params(const slim_map_params* p) {
   }
   if (p->image_width < 0 || p->image_width > 65536)
     return fail(SLIM_ERR_ARG, "image_width must be in [0, 65536]");
+
   return SLIM_OK;
 }
 
@@ -232,9 +233,11 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   }
   m->tile_points = closed_tile_points(m->cap, m->band_blocks);
   m->hash_tile = p->tile_points > 0 ? p->tile_points : 256;
+  // soft counts: the sort tiles sum each voxel's pairs of a tile on chip
+  // before their 2 + K integer reductions (AUTO); direct only on request or
+  // for the weighted variant
   m->direct = p->mode == SLIM_CLOSED_LATEST || p->weighting == SLIM_WEIGHT_LINEAR ||
-              (p->mode == SLIM_CLOSED_SOFT &&
-               (p->aggregation == SLIM_AGG_DIRECT || p->aggregation == SLIM_AGG_AUTO)) ||
+              (p->mode == SLIM_CLOSED_SOFT && p->aggregation == SLIM_AGG_DIRECT) ||
               (p->mode == SLIM_CLOSED_ONEHOT &&
                (p->aggregation == SLIM_AGG_DIRECT ||
                 (p->aggregation == SLIM_AGG_AUTO && p->tile_points == 0)));
@@ -262,9 +265,9 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
               : p->mode == SLIM_CLOSED_SOFT ? kRecSoftFx
                                             : kRecLatest;
   if (m->mode != SLIM_OPEN) {
-    if ((s = m->alloc(&mv.rec, bc * kBlockVoxels * (uint64_t)m->rs)) != SLIM_OK) return bail(s);
     // the pool stays zero beyond the allocation counter (reset re-zeroes
     // the used part), so kernels never zero a block they create
+    if ((s = m->alloc(&mv.rec, bc * kBlockVoxels * (uint64_t)m->rs)) != SLIM_OK) return bail(s);
     if (cudaMemset(mv.rec, 0, bc * kBlockVoxels * (uint64_t)m->rs * sizeof(float)) != cudaSuccess)
       return bail(cuda_fail(cudaGetLastError(), "cudaMemset"));
   } else {
@@ -289,6 +292,9 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
       if ((s = m->alloc(&abf, rc * m->L * 2)) != SLIM_OK) return bail(s);
       m->qscratch.abf = abf;
       if ((s = m->alloc(&m->qscratch.rnorm2, rc)) != SLIM_OK) return bail(s);
+      // the update kernel keeps the BF16 copy of every mean it writes
+      mv.mbf = abf;
+      mv.mbf_norm2 = m->qscratch.rnorm2;
     }
     if ((s = open_alloc_scratch(m, m->open)) != SLIM_OK) return bail(s);
     m->open.tw_log2 = p->tile_points == 8 ? 3 : (p->tile_points == 32 ? 5 : 4);
@@ -357,7 +363,8 @@ slim_status slim_map_reset(slim_map* m, void* stream) {
   const size_t nh = (size_t)m->n_entries;
   const int tok = prof_begin(m, SLIM_KERNEL_RESET, st);
   if (m->mode != SLIM_OPEN)
-    SLIM_CUDA(launch_zero_used_blocks(m->mv, st));
+    SLIM_CUDA(launch_zero_used_blocks(m->mv.rec, m->mv.ctr + kCtrBlocks, m->mv.block_cap, m->rs,
+                                      st));
   else
     SLIM_CUDA(launch_reset_vox_rows(m->mv, st));
   prof_end(m, tok, st);

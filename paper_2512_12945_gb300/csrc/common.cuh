@@ -69,6 +69,8 @@ struct MapView {
   void* mrow;           // [row_cap * L] f32 or bf16 NIG mean
   void* brow;           // [row_cap * L] f32 or bf16 NIG beta
   float* mnorm2;        // [row_cap] |m|^2 of the stored mean (query read-out)
+  void* mbf;            // FP32 storage: [row_cap * L] bf16 copy of m (query operand)
+  float* mbf_norm2;     // FP32 storage: [row_cap] |bf16(m)|^2
   uint32_t row_cap;
 };
 

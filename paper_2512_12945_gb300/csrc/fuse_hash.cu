@@ -360,23 +360,24 @@ cudaError_t hash_setup_attributes() {
   return e;
 }
 
-// Keeps the record pool zero beyond the allocation counter: zeroes the
-// records of blocks [0, min(allocated, capacity)) so that a reset map hands
-// out zeroed blocks (the pool is zeroed once when the map is created).
-__global__ void __launch_bounds__(256) k_zero_used_blocks(float4* rec, const uint32_t* ctr,
+// Keeps a record pool zero beyond its allocation counter: zeroes the records
+// of blocks [0, min(*nblocks, capacity)) so that a reset map hands out zeroed
+// blocks (a pool is zeroed once when the map is created).
+__global__ void __launch_bounds__(256) k_zero_used_blocks(float4* rec, const uint32_t* nblocks,
                                                           uint32_t block_cap, int rs) {
-  const uint32_t nb = min(*(volatile const uint32_t*)&ctr[kCtrBlocks], block_cap);
+  const uint32_t nb = min(*(volatile const uint32_t*)nblocks, block_cap);
   const size_t n4 = (size_t)nb * kBlockVoxels * (size_t)rs / 4;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
        i += (size_t)gridDim.x * blockDim.x)
     rec[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-cudaError_t launch_zero_used_blocks(const MapView& mv, cudaStream_t st) {
-  if (!mv.rec) return cudaSuccess;
+cudaError_t launch_zero_used_blocks(float* rec, const uint32_t* nblocks, uint32_t block_cap,
+                                    int rs, cudaStream_t st) {
+  if (!rec) return cudaSuccess;
   const int sms = g_sms > 0 ? g_sms : 152;
-  k_zero_used_blocks<<<(unsigned)(sms * 8), 256, 0, st>>>(reinterpret_cast<float4*>(mv.rec), mv.ctr,
-                                                       mv.block_cap, mv.rs);
+  k_zero_used_blocks<<<(unsigned)(sms * 8), 256, 0, st>>>(reinterpret_cast<float4*>(rec), nblocks,
+                                                       block_cap, rs);
   return cudaGetLastError();
 }
 

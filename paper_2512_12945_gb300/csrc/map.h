@@ -32,6 +32,7 @@ struct slim_map {
   int hash_tile = 256;  // threads (points) per CTA of the hash-aggregation kernel
   bool direct = false;  // closed one-hot: direct per-pair reductions instead of hash tiles
   int32_t* render_bounds = nullptr;  // slim_render: block bounding box (6 ints)
+
   uint64_t n_entries = 0;
   slim::MapView mv{};
   std::vector<void*> allocs;

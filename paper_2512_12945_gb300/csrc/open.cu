@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(256) k_open_apply(const __grid_constant__ Open
         const float inv = 1.0f / Wn;
         const bool seen = sw.y > 0.f;
         const size_t rb = (size_t)row * L;
-        float nrm = 0.f;
+        float nrm = 0.f, nbf = 0.f;
         for (int e = 4 * (int)lane; e < L; e += 128) {
           float4* a4 = reinterpret_cast<float4*>(h + 4 + 2 * e);          // high halves
           float4* c4 = reinterpret_cast<float4*>(h + 4 + 2 * L + 2 * e);  // low halves
@@ -605,15 +605,24 @@ __global__ void __launch_bounds__(256) k_open_apply(const __grid_constant__ Open
           float4 mo = make_float4(mv4[0], mv4[1], mv4[2], mv4[3]);
           store4<BF16>(mv.mrow, rb + e, mo);
           store4<BF16>(mv.brow, rb + e, make_float4(bv4[0], bv4[1], bv4[2], bv4[3]));
+          if (!BF16) {  // the query's BF16 copy of the FP32 mean, and its norm
+            store4<1>(mv.mbf, rb + e, mo);
+            const float4 q4 = load4<1>(mv.mbf, rb + e);
+            nbf += q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+          }
           if (BF16) mo = load4<BF16>(mv.mrow, rb + e);  // norm of the stored values
           nrm += mo.x * mo.x + mo.y * mo.y + mo.z * mo.z + mo.w * mo.w;
           a4[0] = a4[1] = c4[0] = c4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xFFFFFFFFu, nrm, off);
+        for (int off = 16; off > 0; off >>= 1) {
+          nrm += __shfl_xor_sync(0xFFFFFFFFu, nrm, off);
+          nbf += __shfl_xor_sync(0xFFFFFFFFu, nbf, off);
+        }
         if (lane == 0) {
           mv.tsdf[row] = make_float2(sw.x + unfx32(dq), Wn);
           mv.mnorm2[row] = nrm;
+          if (!BF16) mv.mbf_norm2[row] = nbf;
           reinterpret_cast<float4*>(h)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       } else {

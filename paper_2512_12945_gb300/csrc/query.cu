@@ -541,29 +541,6 @@ __global__ void k_row_norms_bf16(const __nv_bfloat16* __restrict__ rows, float* 
   if (lane == 0) norm2[row] = s;
 }
 
-// FP32-stored means -> BF16 copy for the tensor cores, with |m|^2 of the
-// rounded row (so the cosine is that of the vector the tensor cores see).
-// One warp per row.
-__global__ void k_rows_to_bf16(const float* __restrict__ in, __nv_bfloat16* out, float* norm2,
-                               uint32_t rows, int L) {
-  const uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= rows) return;
-  float s = 0.f;
-  for (int e = 4 * lane; e < L; e += 128) {
-    const float4 v = *reinterpret_cast<const float4*>(in + (size_t)row * L + e);
-    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
-    const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
-    *reinterpret_cast<__nv_bfloat162*>(out + (size_t)row * L + e) = a;
-    *reinterpret_cast<__nv_bfloat162*>(out + (size_t)row * L + e + 2) = b;
-    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-    s += fa.x * fa.x + fa.y * fa.y + fb.x * fb.x + fb.y * fb.y;
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
-  if (lane == 0) norm2[row] = s;
-}
-
 static bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows,
                       uint32_t box_inner, uint32_t box_rows) {
   auto fn = get_encode();
@@ -599,10 +576,7 @@ slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float tempe
   const void* A = m->mv.mrow;
   const float* rn2 = m->mv.mnorm2;
   int tok = prof_begin(m, SLIM_KERNEL_QUERY, st);
-  if (!m->bf16) {
-    k_rows_to_bf16<<<(unsigned)(((uint64_t)n_rows * 32 + 255) / 256), 256, 0, st>>>(
-        static_cast<const float*>(m->mv.mrow), static_cast<__nv_bfloat16*>(m->qscratch.abf),
-        m->qscratch.rnorm2, n_rows, L);
+  if (!m->bf16) {  // FP32 storage: the BF16 copy the update kernel keeps
     A = m->qscratch.abf;
     rn2 = m->qscratch.rnorm2;
   }

@@ -297,3 +297,4 @@ def test_soft_counts_full_scans(K, agg):
                                     torch.from_numpy(s["sem"]).cuda()) for s in w.scans])
         m.sync()
         compare_closed(to_np(m.extract()), o, "soft")
+
