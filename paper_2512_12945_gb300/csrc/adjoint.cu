@@ -109,7 +109,11 @@ __global__ void __launch_bounds__(256) k_backward(MapView mv, ScanGeom g,
 
 // Closed set: one thread per point (the class gradient of a pair is a
 // K-vector, so a warp per point would repeat the DDA 32 times). The thread
-// owns its output row dL/dsem_j and accumulates into it in pair order.
+// accumulates its output row dL/dsem_j in registers (KMAX >= K, unrolled, so
+// the row never leaves the register file) in pair order, reading each pair's
+// K incoming class gradients as float4 where the row allows, and writes the
+// row once.
+template <int KMAX>
 __global__ void __launch_bounds__(256) k_backward_closed(MapView mv, ScanGeom g,
                                                          const float* __restrict__ pts, int64_t n,
                                                          int K, const float* __restrict__ gD,
@@ -117,8 +121,10 @@ __global__ void __launch_bounds__(256) k_backward_closed(MapView mv, ScanGeom g,
                                                          float* gsem, float* gxyz, int sem_grad) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  float* out = gsem + (size_t)j * K;
-  for (int k = 0; k < K; ++k) out[k] = 0.f;
+  float acc[KMAX];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) acc[k] = 0.f;
+  const bool vec = (K & 3) == 0;
   float gx0 = 0.f, gx1 = 0.f, gx2 = 0.f;
   Ray ry;
   if (ray_setup(g, pts[3 * j], pts[3 * j + 1], pts[3 * j + 2], ry)) {
@@ -134,8 +140,25 @@ __global__ void __launch_bounds__(256) k_backward_closed(MapView mv, ScanGeom g,
       const size_t vox = (size_t)slot * kBlockVoxels + local_index(i0, i1, i2);
       const float Wv = rec_weight(mv.rec + vox * mv.rs, mv.K, mv.layout);
       const float invW = 1.0f / Wv;
-      if (sem_grad)
-        for (int k = 0; k < K; ++k) out[k] += gS[vox * (size_t)K + k];
+      if (sem_grad) {
+        const float* row = gS + vox * (size_t)K;
+        if (vec) {
+#pragma unroll
+          for (int k = 0; k < KMAX; k += 4) {
+            if (k < K) {
+              const float4 v = __ldg(reinterpret_cast<const float4*>(row + k));
+              acc[k] += v.x;
+              acc[k + 1] += v.y;
+              acc[k + 2] += v.z;
+              acc[k + 3] += v.w;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < KMAX; ++k)
+            if (k < K) acc[k] += __ldg(row + k);
+        }
+      }
       if (!(d < g.tau)) return;  // clamped at tau: no dependence on x
       const float gd = gD[vox] * invW;
       const float c0 = ((float)i0 + 0.5f) * g.v, c1 = ((float)i1 + 0.5f) * g.v,
@@ -148,6 +171,10 @@ __global__ void __launch_bounds__(256) k_backward_closed(MapView mv, ScanGeom g,
       gx2 += gd * (ry.u2 + (e2 - ry.u2 * eu) * ir);
     });
   }
+  float* out = gsem + (size_t)j * K;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k)
+    if (k < K) out[k] = acc[k];
   gxyz[3 * j + 0] = g.R[0] * gx0 + g.R[3] * gx1 + g.R[6] * gx2;
   gxyz[3 * j + 1] = g.R[1] * gx0 + g.R[4] * gx1 + g.R[7] * gx2;
   gxyz[3 * j + 2] = g.R[2] * gx0 + g.R[5] * gx1 + g.R[8] * gx2;
@@ -169,8 +196,13 @@ slim_status run_backward(slim_map* m, const ScanGeom& g, const float* pts, const
       k_backward<1, 0><<<grid, 256, 0, st>>>(m->mv, g, pts, sem, n, width, gD, gS, gB, gsem, gxyz,
                                              sg);
   } else {
-    k_backward_closed<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->mv, g, pts, n, width, gD,
-                                                                   gS, gsem, gxyz, sg);
+    const unsigned cg = (unsigned)((n + 255) / 256);
+    if (width <= 16)
+      k_backward_closed<16><<<cg, 256, 0, st>>>(m->mv, g, pts, n, width, gD, gS, gsem, gxyz, sg);
+    else if (width <= 32)
+      k_backward_closed<32><<<cg, 256, 0, st>>>(m->mv, g, pts, n, width, gD, gS, gsem, gxyz, sg);
+    else
+      k_backward_closed<64><<<cg, 256, 0, st>>>(m->mv, g, pts, n, width, gD, gS, gsem, gxyz, sg);
   }
   prof_end(m, tok, st);
   const cudaError_t e = cudaGetLastError();
