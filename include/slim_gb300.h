@@ -47,7 +47,10 @@ typedef enum {
   SLIM_ERR_TIMEOUT = 4,     /* a bounded device-side probe or wait ran out */
   SLIM_ERR_NOMEM = 5,       /* device allocation failed at map creation */
   SLIM_ERR_UNSUPPORTED = 6, /* valid request this map's mode cannot serve */
-  SLIM_ERR_INTERNAL = 7     /* an internal device-side consistency check failed */
+  SLIM_ERR_INTERNAL = 7,    /* an internal device-side consistency check failed */
+  SLIM_ERR_RANGE = 8        /* an input value outside its stated range (open set: an
+                               embedding element beyond embed_bound); the
+                               observations that carried it were not fused */
 } slim_status;
 
 /* Semantic fusion mode. */
@@ -137,6 +140,14 @@ typedef struct {
                               in 16 x 16 pixel tiles; 0 (default): unorganized,
                               tiles of 256 consecutive points. Results do not
                               depend on it. 0 .. 65536 */
+  float embed_bound;       /* SLIM_OPEN: bound B on the magnitude of every
+                              embedding element, |z_e| <= B (default 1: unit-norm
+                              embeddings, as the paper's normalised features).
+                              The per-call sums of each voxel's observations
+                              about its stored mean are accumulated exactly, as
+                              64-bit integers in units of B 2^-32 (first moments)
+                              and B^2 2^-31 (second moments); an embedding beyond
+                              B raises SLIM_ERR_RANGE. 2^-16 .. 2^16 */
 } slim_map_params;
 
 typedef struct slim_map slim_map;

@@ -113,6 +113,7 @@ slim_status status_of(uint32_t s) {
   if (s == 0) return SLIM_OK;
   const char* what = s == kDevCapacity ? "device capacity exhausted (blocks, voxels or hash)"
                      : s == kDevTimeout ? "a bounded device wait ran out"
+                     : s == kDevRange   ? "an embedding element beyond the map's embed_bound"
                                         : "device consistency check failed";
   g_err = std::string("sticky map status: ") + what;
   return (slim_status)s;
@@ -136,6 +137,8 @@ slim_status check_params(const slim_map_params* p) {
       return fail(SLIM_ERR_ARG, "embed_storage must be 0 (f32) or 1 (bf16)");
     if (p->voxel_capacity < 1 || p->voxel_capacity > (int64_t)0x7FFFFFFF)
       return fail(SLIM_ERR_ARG, "voxel_capacity must be in [1, 2^31)");
+    if (!(p->embed_bound >= 0x1p-16f && p->embed_bound <= 0x1p16f))
+      return fail(SLIM_ERR_ARG, "embed_bound must be in [2^-16, 2^16]");
   }
   if (!(p->alpha0 >= 0.0) || !std::isfinite(p->alpha0))
     return fail(SLIM_ERR_ARG, "alpha0 must be finite and >= 0");
@@ -202,6 +205,7 @@ slim_status slim_map_params_default(slim_map_params* p) {
   p->hash_capacity = 262144;
   p->voxel_capacity = 1000000;
   p->max_points = 1 << 18;
+  p->embed_bound = 1.0f;
   return SLIM_OK;
 }
 

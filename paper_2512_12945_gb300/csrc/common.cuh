@@ -36,7 +36,8 @@ enum DevStatus : uint32_t {
   kDevOk = 0,
   kDevCapacity = 3,
   kDevTimeout = 4,
-  kDevInternal = 7
+  kDevInternal = 7,
+  kDevRange = 8
 };
 
 // Record the first device fault of a map (later faults keep the first).
@@ -173,9 +174,36 @@ __device__ __forceinline__ void red_add_u64(unsigned long long* a, unsigned long
   asm volatile("red.global.add.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
 }
 
+// x rounded to the nearest integer (ties to even), as int64: the same value
+// as __float2ll_rn(x), from FP32 additions and 32-bit integer operations
+// (the hardware 64-bit conversion runs at the FP64 rate, about 2 per clock
+// per SM on this part). With M = 1.5 2^23, adding M to a float of magnitude
+// below 2^22 leaves its nearest integer in the low mantissa bits; x splits
+// exactly as h 2^20 + l with h = rint(x 2^-20) and |l| <= 2^19, so rint(x) =
+// h 2^20 + rint(l). Values of magnitude 2^41 or more take the hardware path.
+__device__ __forceinline__ long long f2ll_fast(float x) {
+  if (!(fabsf(x) < 0x1p41f)) return __float2ll_rn(x);
+  const float M = 12582912.0f;
+  const float hs = __fadd_rn(__fmul_rn(x, 0x1p-20f), M);
+  const float l = __fmaf_rn(-__fsub_rn(hs, M), 1048576.0f, x);
+  const int ih = __float_as_int(hs) - 0x4B400000;
+  const int il = __float_as_int(__fadd_rn(l, M)) - 0x4B400000;
+  return (long long)ih * 1048576ll + (long long)il;
+}
+
+// v as float from two 32-bit conversions and one FMA: v = h 2^32 + l with l
+// the signed low word (-2^31 <= l < 2^31), so values below 2^31 in
+// magnitude convert exactly rounded and larger ones within about 2^-22
+// relative (not always the nearest float).
+__device__ __forceinline__ float ll2f_fast(long long v) {
+  const int l = (int)(unsigned)v;
+  const int h = (int)((v - (long long)l) >> 32);
+  return __fmaf_rn(__int2float_rn(h), 4294967296.0f, __int2float_rn(l));
+}
+
 // x in fixed point of unit 2^-32 (two's complement bits).
 __device__ __forceinline__ unsigned long long fx32(float x) {
-  return (unsigned long long)__float2ll_rn(__fmul_rn(x, kFxScale));
+  return (unsigned long long)f2ll_fast(__fmul_rn(x, kFxScale));
 }
 __device__ __forceinline__ float unfx32(long long q) {
   return __fmul_rn(__ll2float_rn(q), 1.0f / kFxScale);

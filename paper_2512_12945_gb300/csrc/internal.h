@@ -54,11 +54,12 @@ int closed_tile_points(int cap, int band_blocks);
 int max_band_blocks();
 
 // open.cu: open-set integration by tiles of pixels aggregated on chip.
-// Per-row accumulators of one integration call of a map:
-//   rows[row * stride]: {sum d (int64, unit 2^-32 m), n (u32), pad,
-//                        (S1, S2) for each of the L elements (high halves),
-//                        the same (low halves: rounding errors of the
-//                        additions into the high halves)}
+// Per-row accumulators of one integration call of a map (exact integer
+// sums, zero between calls):
+//   rows[row * stride]: {sum d (int64, unit tau 2^-22), n (u32), pad,
+//                        S1 of the L elements (int64, unit B 2^-32),
+//                        S2 of the L elements (int64, unit B^2 2^-31)}
+// with B the map's embed_bound.
 struct OpenAcc {
   float* rows;      // [row_cap * stride], zero between calls
   uint32_t* listed; // [row_cap] 1 while the row is in list (cleared by the update)
@@ -77,6 +78,7 @@ struct OpenJob {  // 64-byte aligned by its tensor map
   int32_t L;
   int32_t width;        // organized frames: pixels per image row; 0: unorganized
   int32_t tw_log2;      // organized frames: log2 of the tile width (3, 4, 5)
+  float fx1, fx2;       // fixed-point scales of S1 and S2: 2^32 / B, 2^31 / B^2
   uint32_t tiles_x;     // set by launch_open_tiles
   uint32_t tile_begin;  // set by launch_open_tiles
 };
@@ -90,6 +92,8 @@ struct OpenApplyJob {
   MapView mv;
   OpenAcc acc;
   int32_t L;
+  float dunit;  // metres per unit of the accumulated sum of d: tau 2^-22
+  float u1, u2; // units of the accumulated S1 and S2: B 2^-32, B^2 2^-31
 };
 struct OpenApplyBatch {
   OpenApplyJob job[kMaxOpenJobs];

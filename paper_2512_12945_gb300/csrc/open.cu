@@ -43,8 +43,15 @@ constexpr int kOT = 256;          // pixels per tile
 constexpr int kORowPts = 16;      // points per staged row of unorganized tiles
 constexpr int kOE = 64;           // embedding elements per staged chunk
 constexpr int kOMaxTV = 256;      // distinct voxels per tile part
-constexpr int kOTbl = 1024;       // voxel table entries (power of two)
+constexpr int kOTbl = 512;        // voxel table entries (power of two)
+constexpr int kOPList = 4096;     // pixel-list entries per part (more: the part splits)
+constexpr int kOPiece = 64;       // pixels per piece of a voxel's list (a multiple of 4)
+constexpr int kOMaxPc = kOMaxTV + kOPList / kOPiece;  // pieces per part
 constexpr int kOThreads = 256;
+// Points of one map per integration call: each piece adds at most 2^39
+// units to a voxel's S1 and S2 (|z - s| <= 2B over <= 64 pixels), so 2^23
+// pieces keep every exact 64-bit sum below 2^62.
+constexpr int64_t kOpenMaxCallPoints = (int64_t)1 << 23;
 constexpr int32_t kPendingRow = -2;  // vox_row: being created by another CTA
 constexpr int32_t kFailRow = -3;     // vox_row: creation failed (capacity)
 
@@ -71,6 +78,11 @@ __device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
   asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
   uint64_t d;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
@@ -83,37 +95,19 @@ __device__ __forceinline__ uint64_t f2_pack(float x, float y) {
   return (uint64_t)__float_as_uint(x) | ((uint64_t)__float_as_uint(y) << 32);
 }
 
-__device__ __forceinline__ void red_add_v4_nc(float* r, float a, float b, float c, float d) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(r), "f"(a), "f"(b),
-               "f"(c), "f"(d)
+// 8 (FP32) or 4 (BF16) bytes from global to shared memory, asynchronously.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES)
                : "memory");
 }
-
-// old = *r; *r += (a, b, c, d), returning old (16-byte aligned).
-__device__ __forceinline__ float4 atom_add_v4(float* r, float a, float b, float c, float d) {
-  float4 o;
-  asm volatile("atom.global.add.v4.f32 {%0, %1, %2, %3}, [%4], {%5, %6, %7, %8};"
-               : "=f"(o.x), "=f"(o.y), "=f"(o.z), "=f"(o.w)
-               : "l"(r), "f"(a), "f"(b), "f"(c), "f"(d)
-               : "memory");
-  return o;
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
-
-// Rounding error of the addition old + x (Knuth's TwoSum with every
-// operation rounded on its own): (old + x) - fl(old + x), exactly.
-__device__ __forceinline__ float two_sum_err(float old, float x) {
-  const float t = __fadd_rn(old, x);
-  const float z = __fsub_rn(t, old);
-  return __fadd_rn(__fsub_rn(old, __fsub_rn(t, z)), __fsub_rn(x, z));
-}
-
-// Compensated (Kahan) step of a packed pair of sums: sum += y with the
-// running compensation c (sum - c tracks the exact sum to one rounding).
-__device__ __forceinline__ void f2_kahan(uint64_t& sum, uint64_t& c, uint64_t y) {
-  const uint64_t yc = f2_sub(y, c);
-  const uint64_t t = f2_add(sum, yc);
-  c = f2_sub(f2_sub(t, sum), yc);
-  sum = t;
+__device__ __forceinline__ uint64_t lds_u64(uint32_t a) {
+  uint64_t v;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
+  return v;
 }
 
 __device__ __forceinline__ void red_add_u32(uint32_t* a, uint32_t v) {
@@ -133,6 +127,14 @@ __device__ __forceinline__ void tma_load_2d_stream(uint32_t dst, const CUtensorM
       ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
       : "memory");
+}
+
+// Bring a tensor-map box into L2 (no shared memory, no completion).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int32_t x, int32_t y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
 }
 
 __device__ __forceinline__ uint64_t evict_first_policy() {
@@ -210,23 +212,40 @@ __device__ __forceinline__ int64_t tile_row_point(const OpenJob& J, uint32_t lt,
 struct OpenTileSmem {
   float stage[kOT * kOE];          // one chunk of every pixel's embedding
   uint64_t tbl_key[kOTbl];         // voxel key table
+  uint32_t tbl_cnt[kOTbl];         // pixels per table entry
   uint16_t tbl_tv[kOTbl];          // table entry -> dense tile voxel
   uint64_t tv_key[kOMaxTV];
-  unsigned long long tv_dq[kOMaxTV];  // sum of d, fixed point 2^-32 m
-  uint32_t tv_mask[kOMaxTV][kOT / 32];
-  uint32_t tv_off[kOMaxTV];        // start of the voxel's pixel list in plist
-  uint16_t plist[kOT * 27];        // per voxel: its pixels' stage offsets (floats / 2)
-  uint32_t tv_n[kOMaxTV];
+  int32_t tv_dq[kOMaxTV];          // sum of d in units of tau 2^-22 (exact: |sum| < 2^30)
+  uint32_t tv_off[kOMaxTV];        // start of the voxel's pixel list (a multiple of 4)
+  uint32_t tv_n[kOMaxTV];          // pixels of the voxel
+  uint32_t tv_cur[kOMaxTV];        // list fill cursor
   int32_t tv_row[kOMaxTV];
   uint32_t tv_flag[kOMaxTV];       // 1: row created here, 2: wait for another CTA
-  uint16_t order[kOMaxTV];         // tile voxels by decreasing pixel count
+  uint32_t piece[kOMaxPc];         // pieces, longest first (piece_rec)
+  uint32_t pbin[kOPiece / 4];      // partial pieces per length in groups of 4
+  uint32_t work[16];               // per chunk: next quad of pieces for a warp
+  uint64_t shv[kOThreads / 32][4][32];  // per warp: its quad's row shifts (element pairs)
+  // per voxel: its pixels' stage offsets (in 8-byte words), padded to a
+  // multiple of 4 entries with the list's first pixel
+  __align__(16) uint32_t plist[kOPList];
   uint32_t scan[kOThreads / 32];
   uint32_t misc[2];                // 0 status, 1 table overflow
-  uint32_t work[16];               // per chunk: next tile voxel for a warp
   uint32_t rowmask;                // staged rows holding a valid pixel
   int32_t parts[2 * 16];           // pending pixel ranges
   unsigned long long bar;
 };
+
+
+// Two CTAs per SM: 228 KB of shared memory per SM, 1 KB reserved per CTA,
+// plus the 1 KB alignment slack of the dynamic allocation.
+static_assert(sizeof(OpenTileSmem) + 1024 <= (228 * 1024) / 2 - 1024,
+              "k_open_tile needs two CTAs per SM");
+
+// A piece of a voxel's pixel list: tile voxel v, first group of 4 entries
+// g0, groups ng, pixels n (the last group may hold padding).
+__device__ __forceinline__ uint32_t piece_rec(uint32_t v, uint32_t g0, uint32_t ng, uint32_t n) {
+  return v | (g0 << 8) | (ng << 14) | (n << 19);
+}
 
 // Insert a voxel key into the tile table; returns its entry, or -1 when the
 // table is full.
@@ -273,6 +292,12 @@ __device__ __forceinline__ void issue_chunk(OpenTileSmem& s, const OpenJob& J, u
     tma_load_2d_stream(smem_u32(&s.stage[r * rl * kOE]), &J.sem_map, c * kOE, (int32_t)y, bar,
                        policy);
   }
+  // keep the next two chunks on their way into L2 (64 KB per chunk and
+  // CTA): their stage copies then read L2 instead of waiting on HBM
+  const int cn = c == 0 ? 1 : c + 2;
+  for (int k = cn; k <= c + 2 && k * kOE < J.L; ++k)
+    for (int r = 0; r < nr; ++r)
+      if ((rm >> r) & 1u) tma_prefetch_2d(&J.sem_map, k * kOE, (int32_t)tile_row_point(J, lt, r));
 }
 
 template <int BF16>
@@ -303,8 +328,11 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
   if (s.misc[0]) return;
   // this thread's pixel and ray; the staged rows that hold a valid pixel
   const int64_t pj = tid < kOT ? tile_point(J, lt, tid) : -1;
-  Ray ray0;
-  const bool valid = pj >= 0 && ray_setup_at(J.g, J.pts, pj, ray0);
+  bool valid;
+  {
+    Ray ry;  // set up again by each walk (fewer registers held across the part)
+    valid = pj >= 0 && ray_setup_at(J.g, J.pts, pj, ry);
+  }
   if (valid) atomicOr(&s.rowmask, 1u << (tid / tile_row_len(J)));
   __syncthreads();
   // chunk 0 is fetched while the rays are walked (it serves every part)
@@ -322,25 +350,34 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
     --nparts;
     const int p0 = s.parts[2 * nparts], p1 = s.parts[2 * nparts + 1];
     const bool mine = valid && tid >= p0 && tid < p1;
-    // 1. the part's distinct voxels
-    for (int e = tid; e < kOTbl; e += kOThreads) s.tbl_key[e] = kEmptyKey;
+    // 1. the part's distinct voxels and their pixel counts
+    for (int e = tid; e < kOTbl; e += kOThreads) {
+      s.tbl_key[e] = kEmptyKey;
+      s.tbl_cnt[e] = 0u;
+    }
     if (tid == 0) s.misc[1] = 0;
     __syncthreads();
     if (mine) {
-      Ray ry = ray0;
+      Ray ry;
+      ray_setup_at(J.g, J.pts, pj, ry);
       ray_for_each(J.g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float) {
-        if (tbl_insert(s, pack_voxel(i0, i1, i2)) < 0) s.misc[1] = 1;
+        const int e = tbl_insert(s, pack_voxel(i0, i1, i2));
+        if (e < 0)
+          s.misc[1] = 1;
+        else
+          atomicAdd(&s.tbl_cnt[e], 1u);
       });
     }
     __syncthreads();
-    // 2. dense ids (4 table entries per thread)
+    // 2. dense ids (2 table entries per thread)
+    constexpr int kPer = kOTbl / kOThreads;
     uint32_t occ = 0;
 #pragma unroll
-    for (int k = 0; k < kOTbl / kOThreads; ++k) occ += s.tbl_key[tid * 4 + k] != kEmptyKey;
+    for (int k = 0; k < kPer; ++k) occ += s.tbl_cnt[tid * kPer + k] != 0u;
     uint32_t ntv;
-    uint32_t off = cta_exclusive_scan(occ, s.scan, &ntv);
+    uint32_t id = cta_exclusive_scan(occ, s.scan, &ntv);
     if (ntv > (uint32_t)kOMaxTV || s.misc[1]) {
-      // too many voxels for the tables: split the part in two
+      // too many voxels for the tables: split the part
       __syncthreads();
       if (tid == 0) {
         const int mid = (p0 + p1) / 2;
@@ -354,40 +391,94 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
       continue;
     }
 #pragma unroll
-    for (int k = 0; k < kOTbl / kOThreads; ++k) {
-      const int e = tid * 4 + k;
-      const uint64_t key = s.tbl_key[e];
-      if (key != kEmptyKey) {
-        s.tbl_tv[e] = (uint16_t)off;
-        s.tv_key[off] = key;
-        ++off;
+    for (int k = 0; k < kPer; ++k) {
+      const int e = tid * kPer + k;
+      const uint32_t c = s.tbl_cnt[e];
+      if (c) {
+        s.tbl_tv[e] = (uint16_t)id;
+        s.tv_key[id] = s.tbl_key[e];
+        s.tv_n[id] = c;
+        s.tv_cur[id] = 0u;
+        s.tv_dq[id] = 0;
+        s.tv_flag[id] = 0u;
+        ++id;
       }
     }
     if (tid < 16) s.work[tid] = 0u;
-    for (int v = tid; v < (int)ntv; v += kOThreads) {
-      s.tv_n[v] = 0;
-      s.tv_dq[v] = 0ull;
-      s.tv_flag[v] = 0;
-#pragma unroll
-      for (int w = 0; w < kOT / 32; ++w) s.tv_mask[v][w] = 0u;
-    }
     __syncthreads();
-    // 3. pixel masks, counts and fixed-point sums of d
+    // 3. list offsets (each voxel's list padded to a multiple of 4 entries)
+    //    and the pieces: every list cut into pieces of at most kOPiece
+    //    pixels, longest first (full pieces, then the rest by length), so
+    //    that quads of consecutive pieces cost about the same
+    {
+      const uint32_t n = tid < (int)ntv ? s.tv_n[tid] : 0u;
+      const uint32_t full = n / kOPiece, rest = n % kOPiece;
+      const uint32_t packed = ((n + 3u) & ~3u) | (full << 20);
+      if (tid < 16) s.pbin[tid] = 0u;
+      uint32_t tot;
+      const uint32_t pre = cta_exclusive_scan(packed, s.scan, &tot);
+      const uint32_t nfull = tot >> 20;
+      if ((tot & 0xFFFFFu) > (uint32_t)kOPList) {
+        // too many list entries: split the part
+        if (tid == 0) {
+          const int mid = (p0 + p1) / 2;
+          s.parts[2 * nparts] = p0;
+          s.parts[2 * nparts + 1] = mid;
+          s.parts[2 * nparts + 2] = mid;
+          s.parts[2 * nparts + 3] = p1;
+        }
+        nparts += 2;
+        __syncthreads();
+        continue;
+      }
+      if (tid < (int)ntv) {
+        s.tv_off[tid] = pre & 0xFFFFFu;
+        for (uint32_t k = 0; k < full; ++k)
+          s.piece[(pre >> 20) + k] = piece_rec(tid, k * (kOPiece / 4), kOPiece / 4, kOPiece);
+        if (rest) atomicAdd(&s.pbin[(rest + 3u) / 4u - 1u], 1u);
+      }
+      __syncthreads();
+      if (tid == 0) {  // bins of the partial pieces, longest first
+        uint32_t at = nfull;
+        for (int b = kOPiece / 4 - 1; b >= 0; --b) {
+          const uint32_t c = s.pbin[b];
+          s.pbin[b] = at;
+          at += c;
+        }
+        s.misc[1] = at;  // pieces of the part
+      }
+      __syncthreads();
+      if (tid < (int)ntv && rest) {
+        const uint32_t g = (rest + 3u) / 4u;
+        s.piece[atomicAdd(&s.pbin[g - 1u], 1u)] = piece_rec(tid, full * (kOPiece / 4), g, rest);
+      }
+    }
+    const uint32_t npc = s.misc[1];
+    __syncthreads();
+    // 4. pixel lists and fixed-point sums of d
     if (mine) {
-      Ray ry = ray0;
+      Ray ry;
+      ray_setup_at(J.g, J.pts, pj, ry);
+      const uint32_t so = (uint32_t)tid * (kOE / 2);  // the pixel's stage row, 8-byte words
+      const float dsc = __fdiv_rn(4194304.0f, J.g.tau);
       ray_for_each(J.g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d) {
-        const int e = tbl_find(s, pack_voxel(i0, i1, i2));
-        const int v = s.tbl_tv[e];
-        atomicOr(&s.tv_mask[v][tid >> 5], 1u << (tid & 31));
-        atomicAdd(&s.tv_n[v], 1u);
-        atomicAdd(&s.tv_dq[v], fx32(d));
+        const int v = s.tbl_tv[tbl_find(s, pack_voxel(i0, i1, i2))];
+        s.plist[s.tv_off[v] + atomicAdd(&s.tv_cur[v], 1u)] = so;
+        atomicAdd(&s.tv_dq[v], __float2int_rn(__fmul_rn(d, dsc)));
       });
     }
     __syncthreads();
-    // 4. blocks and rows: find, or create (a new row gets its shift and
-    //    zero (S, W) before it is published), or wait for another CTA's
+    // 5. list padding (with the first pixel of the list's last piece, whose
+    //    deviation from that piece's shift is exactly zero); blocks and rows:
+    //    find, or create (a new row gets its shift and zero (S, W) before it
+    //    is published), or wait for another CTA's
     int32_t* vr = nullptr;
     if (tid < (int)ntv) {
+      const uint32_t o = s.tv_off[tid], n = s.tv_n[tid];
+      if (n & 3u) {
+        const uint32_t f = s.plist[o + (n / kOPiece) * kOPiece];
+        for (uint32_t j = n; j & 3u; ++j) s.plist[o + j] = f;
+      }
       int32_t i0, i1, i2;
       unpack_voxel(s.tv_key[tid], i0, i1, i2);
       const uint32_t slot = map_block_slot(mv, pack_block(i0 >> 3, i1 >> 3, i2 >> 3));
@@ -413,15 +504,11 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
       s.tv_row[tid] = row;
     }
     __syncthreads();
-    // the shift of each row created here: the embedding of its first pixel
+    // the shift of each row created here: the embedding of its list's first
+    // pixel
     for (int v = (int)warp; v < (int)ntv; v += kOThreads / 32) {
       if (s.tv_flag[v] != 1) continue;
-      int p = 0;
-      for (int w = 0; w < kOT / 32; ++w)
-        if (s.tv_mask[v][w]) {
-          p = 32 * w + __ffs(s.tv_mask[v][w]) - 1;
-          break;
-        }
+      const int p = (int)(s.plist[s.tv_off[v]] / (kOE / 2));
       const int64_t jp = tile_point(J, lt, p);
       const int32_t row = s.tv_row[v];
       const float* src = J.sem + (size_t)jp * L;
@@ -452,43 +539,19 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
       const int32_t row = s.tv_row[tid];
       if (row >= 0 && atomicExch(&J.acc.listed[row], 1u) == 0u)
         J.acc.list[atomicAdd(J.acc.count, 1u)] = (uint32_t)row;
-      // rank by decreasing pixel count (ties by id): the longest voxels first
-      const uint32_t n0 = s.tv_n[tid];
-      int rank = 0;
-      for (int v = 0; v < (int)ntv; ++v) {
-        const uint32_t nv = s.tv_n[v];
-        rank += nv > n0 || (nv == n0 && v < tid);
-      }
-      s.order[rank] = (uint16_t)tid;
-    }
-    // the pixel lists: offsets of the voxels' lists (exclusive scan of the
-    // counts), then one warp per voxel expands its mask, 8 pixels per lane
-    {
-      uint32_t tot;
-      const uint32_t o = cta_exclusive_scan(tid < (int)ntv ? s.tv_n[tid] : 0u, s.scan, &tot);
-      if (tid < (int)ntv) s.tv_off[tid] = o;
-      __syncthreads();
-      for (int v = (int)warp; v < (int)ntv; v += kOThreads / 32) {
-        const uint32_t bits = (s.tv_mask[v][lane >> 2] >> (8 * (lane & 3))) & 0xFFu;
-        uint32_t x = (uint32_t)__popc(bits);
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
-          if ((int)lane >= off) x += y;
-        }
-        uint32_t at = s.tv_off[v] + x - (uint32_t)__popc(bits);
-        uint32_t b = bits;
-        while (b) {
-          const int p = 8 * (int)lane + __ffs(b) - 1;
-          b &= b - 1;
-          s.plist[at++] = (uint16_t)(p * (kOE / 2));
-        }
-      }
     }
     __syncthreads();
-    // 5. per chunk: sums of y = z - s and y^2 over each voxel's pixels, in
-    //    two alternating chains, the sums of y compensated (Kahan); warps
-    //    take voxels (longest first) from a shared counter
+    // 6. per chunk and quad of pieces: each piece's sums of y = z - s_t and
+    //    y^2 over its pixels, about its first pixel s_t (in shared memory),
+    //    the quad's four pieces in lockstep (four independent chains, each
+    //    group of four pixels summed as a tree first); then taken about the
+    //    row's shift s (d = s_t - s, n pixels):
+    //      S1 = S1_t + n d,   S2 = S2_t + d (2 S1_t + n d),
+    //    and added to the row's accumulator exactly, as 64-bit integer
+    //    reductions (no return value, so no round trip holds the warp; the
+    //    quad's four shift loads travel while the sums run). Warps take
+    //    quads (longest first) from a shared counter.
+    const uint32_t nq = (npc + 3u) >> 2;
     for (int c = 0; c < nch; ++c) {
       if (cur != c) {  // the stage is free (barrier at the end of the last chunk)
         if (tid == 0) issue_chunk(s, J, lt, c, policy);
@@ -506,52 +569,116 @@ __global__ void __launch_bounds__(kOThreads, 2) k_open_tile(const __grid_constan
         inflight = false;
       }
       const int e0 = c * kOE + 2 * (int)lane;
+      const uint64_t* st64 = reinterpret_cast<const uint64_t*>(s.stage) + lane;
       for (;;) {
-        uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(&s.work[c], 1u);
-        k = __shfl_sync(0xFFFFFFFFu, k, 0);
-        if (k >= ntv) break;
-        const int v = s.order[k];
-        const int32_t row = s.tv_row[v];
-        if (row < 0) continue;
-        const float2 sh = load2<BF16>(mv.mrow, (size_t)row * L + e0);
-        const uint64_t s2 = f2_pack(sh.x, sh.y);
-        uint64_t a1 = 0, a2 = 0, b1 = 0, b2 = 0, ca = 0, cb = 0;
-        const uint64_t* st64 = reinterpret_cast<const uint64_t*>(s.stage) + lane;
-        const uint32_t pb0 = s.tv_off[v], pe = pb0 + s.tv_n[v];
-        uint32_t i = pb0;
-        for (; i + 1 < pe; i += 2) {
-          const uint64_t za = st64[s.plist[i]];
-          const uint64_t zb = st64[s.plist[i + 1]];
-          const uint64_t ya = f2_sub(za, s2), yb = f2_sub(zb, s2);
-          f2_kahan(a1, ca, ya);
-          a2 = f2_fma(ya, ya, a2);
-          f2_kahan(b1, cb, yb);
-          b2 = f2_fma(yb, yb, b2);
+        uint32_t q = 0;
+        if (lane == 0) q = atomicAdd(&s.work[c], 1u);
+        q = __shfl_sync(0xFFFFFFFFu, q, 0);
+        if (q >= nq) break;
+        int32_t row[4];
+        uint32_t pr[4];
+        const uint4* pl[4];
+        uint64_t sl[4], a1[4], a2[4];
+        const uint32_t ng = (s.piece[4 * q] >> 14) & 0x1Fu;  // the quad's longest
+        // the rows' shifts travel to shared memory while the sums run
+        const uint32_t shb = smem_u32(&s.shv[warp][0][lane]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t k = 4 * q + j;
+          pr[j] = k < npc ? s.piece[k] : 0u;  // none: a piece of no groups
+          const int v = (int)(pr[j] & 0xFFu);
+          row[j] = k < npc ? s.tv_row[v] : -1;
+          pl[j] = reinterpret_cast<const uint4*>(s.plist + s.tv_off[v]) + ((pr[j] >> 8) & 0x3Fu);
+          sl[j] = st64[pl[j][0].x];
+          if (row[j] >= 0) {
+            if (BF16)
+              cp_async<4>(shb + 256u * j,
+                          static_cast<const __nv_bfloat16*>(mv.mrow) + (size_t)row[j] * L + e0);
+            else
+              cp_async<8>(shb + 256u * j,
+                          static_cast<const float*>(mv.mrow) + (size_t)row[j] * L + e0);
+          }
+          a1[j] = 0;
+          a2[j] = 0;
         }
-        if (i < pe) {
-          const uint64_t ya = f2_sub(st64[s.plist[i]], s2);
-          f2_kahan(a1, ca, ya);
-          a2 = f2_fma(ya, ya, a2);
+        for (uint32_t gi = 0; gi < ng; ++gi) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (gi >= ((pr[j] >> 14) & 0x1Fu)) continue;  // uniform over the warp
+            const uint4 o = pl[j][gi];
+            const uint64_t ya = f2_sub(st64[o.x], sl[j]), yb = f2_sub(st64[o.y], sl[j]);
+            const uint64_t yc = f2_sub(st64[o.z], sl[j]), yd = f2_sub(st64[o.w], sl[j]);
+            // the group's four terms summed as a tree, then added to the
+            // voxel's running sums (chains of at most 64 additions)
+            a1[j] = f2_add(a1[j], f2_add(f2_add(ya, yb), f2_add(yc, yd)));
+            a2[j] = f2_add(a2[j], f2_add(f2_fma(yb, yb, f2_mul(ya, ya)),
+                                         f2_fma(yd, yd, f2_mul(yc, yc))));
+          }
         }
-        const float2 S1 = f2_unpack(f2_add(f2_sub(a1, ca), f2_sub(b1, cb)));
-        const float2 S2 = f2_unpack(f2_add(a2, b2));
-        // across tiles, compensated: the high half of the accumulator takes
-        // the sums, the low half the exact rounding error of each addition
-        float* hi = J.acc.rows + (size_t)row * J.acc.stride + 4 + 2 * e0;
-        const float4 old = atom_add_v4(hi, S1.x, S2.x, S1.y, S2.y);
-        red_add_v4_nc(hi + 2 * L, two_sum_err(old.x, S1.x), two_sum_err(old.y, S2.x),
-                      two_sum_err(old.z, S1.y), two_sum_err(old.w, S2.y));
+        cp_async_wait_all();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (row[j] < 0) continue;  // uniform over the warp
+          uint64_t sg;
+          if (BF16) {
+            const uint32_t w = (uint32_t)lds_u64(shb + 256u * j);
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+            sg = f2_pack(f.x, f.y);
+          } else {
+            sg = lds_u64(shb + 256u * j);
+          }
+          const uint64_t dl = f2_sub(sl[j], sg);
+          const float nf = (float)(pr[j] >> 19);
+          const uint64_t n2 = f2_pack(nf, nf);
+          const float2 S1 = f2_unpack(f2_fma(n2, dl, a1[j]));
+          const float2 S2 = f2_unpack(f2_fma(dl, f2_fma(n2, dl, f2_add(a1[j], a1[j])), a2[j]));
+          // lane l takes elements c 64 + l and c 64 + 32 + l (held by lanes
+          // l / 2 and 16 + l / 2), so that each reduction below covers 256
+          // contiguous bytes
+          const int h0 = (int)(lane >> 1), h1 = 16 + (int)(lane >> 1);
+          const bool odd = lane & 1u;
+          const float p0x = __shfl_sync(0xFFFFFFFFu, S1.x, h0);
+          const float p0y = __shfl_sync(0xFFFFFFFFu, S1.y, h0);
+          const float p1x = __shfl_sync(0xFFFFFFFFu, S1.x, h1);
+          const float p1y = __shfl_sync(0xFFFFFFFFu, S1.y, h1);
+          const float r0x = __shfl_sync(0xFFFFFFFFu, S2.x, h0);
+          const float r0y = __shfl_sync(0xFFFFFFFFu, S2.y, h0);
+          const float r1x = __shfl_sync(0xFFFFFFFFu, S2.x, h1);
+          const float r1y = __shfl_sync(0xFFFFFFFFu, S2.y, h1);
+          const float p0 = odd ? p0y : p0x, p1 = odd ? p1y : p1x;
+          const float r0 = odd ? r0y : r0x, r1 = odd ? r1y : r1x;
+          // exact across tiles: 64-bit integers in units of B 2^-32 (S1) and
+          // B^2 2^-31 (S2); a piece adds at most 2^39 units when every
+          // element lies within the bound B (anything else, NaN included,
+          // raises the range status and is not added)
+          const float x0 = __fmul_rn(p0, J.fx1), x1 = __fmul_rn(p1, J.fx1);
+          const float y0 = __fmul_rn(r0, J.fx2), y1 = __fmul_rn(r1, J.fx2);
+          const bool ok = fabsf(x0) <= 0x1p39f && fabsf(x1) <= 0x1p39f && fabsf(y0) <= 0x1p39f &&
+                          fabsf(y1) <= 0x1p39f;
+          if (__any_sync(0xFFFFFFFFu, !ok)) {
+            if (lane == 0) raise_status(mv.ctr, kDevRange, 16);
+            continue;
+          }
+          unsigned long long* P1 = reinterpret_cast<unsigned long long*>(
+                                       J.acc.rows + (size_t)row[j] * J.acc.stride + 4) +
+                                   c * kOE + lane;
+          unsigned long long* P2 = P1 + L;
+          red_add_u64(P1, (unsigned long long)f2ll_fast(x0));
+          red_add_u64(P1 + 32, (unsigned long long)f2ll_fast(x1));
+          red_add_u64(P2, (unsigned long long)f2ll_fast(y0));
+          red_add_u64(P2 + 32, (unsigned long long)f2ll_fast(y1));
+        }
       }
       __syncthreads();  // the stage is free again
     }
     if (abort) break;
-    // 6. counts and sums of d
+    // 7. counts and sums of d
     if (tid < (int)ntv) {
       const int32_t row = s.tv_row[tid];
       if (row >= 0) {
         float* h = J.acc.rows + (size_t)row * J.acc.stride;
-        red_add_u64(reinterpret_cast<unsigned long long*>(h), s.tv_dq[tid]);
+        red_add_u64(reinterpret_cast<unsigned long long*>(h),
+                    (unsigned long long)(long long)s.tv_dq[tid]);
         red_add_u32(reinterpret_cast<uint32_t*>(h) + 2, s.tv_n[tid]);
       }
     }
@@ -572,11 +699,15 @@ __global__ void __launch_bounds__(256) k_open_apply(const __grid_constant__ Open
     const MapView& mv = b.job[jb].mv;
     const OpenAcc& A = b.job[jb].acc;
     const int L = b.job[jb].L;
+    const float dunit = b.job[jb].dunit;
+    const float u1 = b.job[jb].u1, u2 = b.job[jb].u2;
     const bool live = *(volatile uint32_t*)&mv.ctr[kCtrStatus] == 0;
     const int64_t cnt = min((int64_t)*A.count, (int64_t)mv.row_cap);
     for (int64_t i = gw; i < cnt; i += nw) {
       const uint32_t row = A.list[i];
       float* h = A.rows + (size_t)row * A.stride;
+      longlong2* P1 = reinterpret_cast<longlong2*>(h + 4);  // S1 plane
+      longlong2* P2 = P1 + L / 2;                          // S2 plane
       if (lane == 0) A.listed[row] = 0u;
       if (live) {
         const long long dq = *reinterpret_cast<const long long*>(h);
@@ -588,12 +719,13 @@ __global__ void __launch_bounds__(256) k_open_apply(const __grid_constant__ Open
         const size_t rb = (size_t)row * L;
         float nrm = 0.f, nbf = 0.f;
         for (int e = 4 * (int)lane; e < L; e += 128) {
-          float4* a4 = reinterpret_cast<float4*>(h + 4 + 2 * e);          // high halves
-          float4* c4 = reinterpret_cast<float4*>(h + 4 + 2 * L + 2 * e);  // low halves
-          const float4 p = a4[0], q = a4[1], pc = c4[0], qc = c4[1];
-          // (S1, S2) of elements e .. e + 3
-          const float s1[4] = {p.x + pc.x, p.z + pc.z, q.x + qc.x, q.z + qc.z};
-          const float s2[4] = {p.y + pc.y, p.w + pc.w, q.y + qc.y, q.w + qc.w};
+          // (S1, S2) of elements e .. e + 3, from their exact integer sums
+          const longlong2 qa = P1[e / 2], qb = P1[e / 2 + 1];
+          const longlong2 ra = P2[e / 2], rb2 = P2[e / 2 + 1];
+          const float s1[4] = {__fmul_rn(ll2f_fast(qa.x), u1), __fmul_rn(ll2f_fast(qa.y), u1),
+                               __fmul_rn(ll2f_fast(qb.x), u1), __fmul_rn(ll2f_fast(qb.y), u1)};
+          const float s2[4] = {__fmul_rn(ll2f_fast(ra.x), u2), __fmul_rn(ll2f_fast(ra.y), u2),
+                               __fmul_rn(ll2f_fast(rb2.x), u2), __fmul_rn(ll2f_fast(rb2.y), u2)};
           const float4 m4 = load4<BF16>(mv.mrow, rb + e);
           const float4 b4 = seen ? load4<BF16>(mv.brow, rb + e) : make_float4(0.f, 0.f, 0.f, 0.f);
           float mv4[4] = {m4.x, m4.y, m4.z, m4.w}, bv4[4] = {b4.x, b4.y, b4.z, b4.w};
@@ -612,7 +744,11 @@ __global__ void __launch_bounds__(256) k_open_apply(const __grid_constant__ Open
           }
           if (BF16) mo = load4<BF16>(mv.mrow, rb + e);  // norm of the stored values
           nrm += mo.x * mo.x + mo.y * mo.y + mo.z * mo.z + mo.w * mo.w;
-          a4[0] = a4[1] = c4[0] = c4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+          const longlong2 z = make_longlong2(0, 0);
+          P1[e / 2] = z;
+          P1[e / 2 + 1] = z;
+          P2[e / 2] = z;
+          P2[e / 2 + 1] = z;
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -620,7 +756,7 @@ __global__ void __launch_bounds__(256) k_open_apply(const __grid_constant__ Open
           nbf += __shfl_xor_sync(0xFFFFFFFFu, nbf, off);
         }
         if (lane == 0) {
-          mv.tsdf[row] = make_float2(sw.x + unfx32(dq), Wn);
+          mv.tsdf[row] = make_float2(__fadd_rn(sw.x, __fmul_rn(ll2f_fast(dq), dunit)), Wn);
           mv.mnorm2[row] = nrm;
           if (!BF16) mv.mbf_norm2[row] = nbf;
           reinterpret_cast<float4*>(h)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -733,6 +869,14 @@ cudaError_t launch_reset_vox_rows(const MapView& mv, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Units of the accumulated S1 and S2 (the reciprocals of the tile kernel's
+// scales, each rounded once).
+static void open_units(const slim_map* m, OpenApplyJob& a) {
+  const double B = (double)m->p.embed_bound;
+  a.u1 = (float)(B / 4294967296.0);
+  a.u2 = (float)(B * B / 2147483648.0);
+}
+
 slim_status open_fill_job(slim_map* m, OpenJob& J, const ScanGeom& g, const float* pts,
                           const float* sem, int64_t n, int width) {
   J.mv = m->mv;
@@ -744,6 +888,9 @@ slim_status open_fill_job(slim_map* m, OpenJob& J, const ScanGeom& g, const floa
   J.L = m->L;
   J.width = width;
   J.tw_log2 = m->open.tw_log2;
+  const double B = (double)m->p.embed_bound;
+  J.fx1 = (float)(4294967296.0 / B);
+  J.fx2 = (float)(2147483648.0 / (B * B));
   if (!open_encode_sem(&J.sem_map, sem, n, m->L, width > 0 ? 1 << J.tw_log2 : kORowPts))
     return fail(SLIM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the embeddings");
   return SLIM_OK;
@@ -752,6 +899,8 @@ slim_status open_fill_job(slim_map* m, OpenJob& J, const ScanGeom& g, const floa
 slim_status open_integrate(slim_map* m, const ScanGeom& g, const float* pts, const float* sem,
                            int64_t n, int width, cudaStream_t st) {
   if (n <= 0) return SLIM_OK;
+  if (n > kOpenMaxCallPoints)
+    return fail(SLIM_ERR_ARG, "open set: at most 2^23 points per map and call");
   OpenBatch b;
   b.n_jobs = 1;
   slim_status s = open_fill_job(m, b.job[0], g, pts, sem, n, width);
@@ -767,6 +916,8 @@ slim_status open_integrate(slim_map* m, const ScanGeom& g, const float* pts, con
   a.job[0].mv = m->mv;
   a.job[0].acc = m->open.acc;
   a.job[0].L = m->L;
+  a.job[0].dunit = (float)m->p.trunc * 0x1p-22f;
+  open_units(m, a.job[0]);
   tok = prof_begin(m, SLIM_KERNEL_OPEN_APPLY, st);
   e = launch_open_apply(a, m->bf16, st);
   prof_end(m, tok, st);
@@ -780,8 +931,17 @@ slim_status open_integrate(slim_map* m, const ScanGeom& g, const float* pts, con
 slim_status open_integrate_batch(const std::vector<OpenItem>& items, cudaStream_t st) {
   if (items.empty()) return SLIM_OK;
   std::vector<slim_map*> maps;
-  for (const OpenItem& it : items)
-    if (std::find(maps.begin(), maps.end(), it.map) == maps.end()) maps.push_back(it.map);
+  std::vector<int64_t> npts;
+  for (const OpenItem& it : items) {
+    const size_t k = std::find(maps.begin(), maps.end(), it.map) - maps.begin();
+    if (k == maps.size()) {
+      maps.push_back(it.map);
+      npts.push_back(0);
+    }
+    npts[k] += std::max<int64_t>(it.n, 0);
+    if (npts[k] > kOpenMaxCallPoints)
+      return fail(SLIM_ERR_ARG, "open set: at most 2^23 points per map and call");
+  }
   for (size_t k = 0; k < maps.size(); ++k) {
     cudaError_t e = cudaMemsetAsync(maps[k]->open.acc.count, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return fail(SLIM_ERR_CUDA, cudaGetErrorString(e));
@@ -831,6 +991,8 @@ slim_status open_integrate_batch(const std::vector<OpenItem>& items, cudaStream_
       a.job[a.n_jobs].mv = m->mv;
       a.job[a.n_jobs].acc = m->open.acc;
       a.job[a.n_jobs].L = m->L;
+      a.job[a.n_jobs].dunit = (float)m->p.trunc * 0x1p-22f;
+      open_units(m, a.job[a.n_jobs]);
       if (++a.n_jobs == kMaxOpenJobs) {
         slim_status s = flush();
         if (s != SLIM_OK) return s;

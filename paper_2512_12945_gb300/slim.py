@@ -46,7 +46,7 @@ class slim_map_params(ctypes.Structure):
                 ("voxel_capacity", ctypes.c_int64), ("max_points", ctypes.c_int64),
                 ("aggregation", ctypes.c_int32), ("tile_points", ctypes.c_int32),
                 ("weighting", ctypes.c_int32), ("weight_eps", ctypes.c_float),
-                ("image_width", ctypes.c_int32)]
+                ("image_width", ctypes.c_int32), ("embed_bound", ctypes.c_float)]
 
 
 class slim_stats(ctypes.Structure):
@@ -374,7 +374,8 @@ class Map:
                  embed_storage="f32", min_range=0.0, max_range=1e30, alpha0=1.0,
                  body_from_sensor=None, block_capacity=100000, hash_capacity=262144,
                  voxel_capacity=1000000, max_points=1 << 18, aggregation="auto",
-                 tile_points=0, weighting="constant", weight_eps=0.0, image_width=0):
+                 tile_points=0, weighting="constant", weight_eps=0.0, image_width=0,
+                 embed_bound=1.0):
         p = slim_map_params_default()
         p.voxel_size = voxel_size
         p.trunc = trunc
@@ -398,6 +399,7 @@ class Map:
         p.weighting = WEIGHTING[weighting] if isinstance(weighting, str) else int(weighting)
         p.weight_eps = weight_eps
         p.image_width = image_width
+        p.embed_bound = embed_bound
         self.params = p
         self.mode = p.mode
         self.width = embed_dim if p.mode == SLIM_OPEN else num_classes

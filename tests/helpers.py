@@ -1,5 +1,7 @@
 """Shared helpers for the GPU parity tests: run the CUDA path and the oracle
 on the same seeded inputs and compare them element by element."""
+import os
+
 import numpy as np
 
 import oracle
@@ -43,12 +45,22 @@ def to_np(ext):
     return {k: v.cpu().numpy() for k, v in ext.items()}
 
 
+# Worst error / tolerance ratio of every assert_close check, per (test, field);
+# printed at the end of the session (conftest.py) so the margin of each
+# parity check is visible, not only its pass or fail.
+MARGINS = {}
+
+
 def assert_close(got, ref, rtol=RTOL, atol=ATOL, what=""):
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
     assert got.shape == ref.shape, (what, got.shape, ref.shape)
     err = np.abs(got - ref)
-    bad = err > atol + rtol * np.abs(ref)
+    tol = atol + rtol * np.abs(ref)
+    if err.size:
+        key = (os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], what)
+        MARGINS[key] = max(MARGINS.get(key, 0.0), float((err / tol).max()))
+    bad = err > tol
     assert not bad.any(), (f"{what}: {int(bad.sum())} of {bad.size} outside rtol={rtol} "
                            f"atol={atol}; worst {err.max():.3g}")
 

@@ -75,13 +75,30 @@ def test_open_ragged_and_empty():
 
 
 def test_open_identical_embeddings_give_zero_beta():
+    """Identical (not normalised) embeddings: beta stays 0 and m = z; the
+    map's embed_bound covers their largest element."""
     w = _work(frames=3)
     z = np.random.default_rng(0).standard_normal(64).astype(np.float32)
     for s in w.scans:
         s["sem"] = np.ascontiguousarray(np.tile(z, (s["pts"].shape[0], 1)))
-    g = to_np(gpu_map(w, voxel_capacity=200000).extract())
+    g = to_np(gpu_map(w, voxel_capacity=200000, embed_bound=4.0).extract())
     assert np.abs(g["beta"]).max() < 1e-6
     assert_close(g["sem"], np.tile(z, (len(g["W"]), 1)), 1e-6, 1e-6, "m")
+
+
+def test_open_embedding_beyond_bound_raises_range():
+    """An embedding element beyond the map's embed_bound (here 10 against
+    the default bound 1) is reported as SLIM_ERR_RANGE; the same scans under
+    a bound that covers them match the oracle."""
+    from paper_2512_12945_gb300 import slim
+    w = _work(frames=2)
+    for s in w.scans:
+        s["sem"] = np.ascontiguousarray(s["sem"] * 10.0, dtype=np.float32)
+    with pytest.raises(slim.SlimError) as e:
+        gpu_map(w, voxel_capacity=200000)
+    assert e.value.status == 8
+    g = to_np(gpu_map(w, voxel_capacity=200000, embed_bound=16.0).extract())
+    _compare(g, oracle_map(w).extract())
 
 
 def test_open_voxel_capacity_fault():
