@@ -269,10 +269,13 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
               : p->mode == SLIM_CLOSED_SOFT ? kRecSoftFx
                                             : kRecLatest;
   if (m->mode != SLIM_OPEN) {
-    // the pool stays zero beyond the allocation counter (reset re-zeroes
-    // the used part), so kernels never zero a block they create
+    // the pool stays zero outside the sub-blocks written since the last
+    // reset (each block's touched mask names them; the reset re-zeroes
+    // those), so kernels never zero a block they create
     if ((s = m->alloc(&mv.rec, bc * kBlockVoxels * (uint64_t)m->rs)) != SLIM_OK) return bail(s);
-    if (cudaMemset(mv.rec, 0, bc * kBlockVoxels * (uint64_t)m->rs * sizeof(float)) != cudaSuccess)
+    if ((s = m->alloc(&mv.blk_mask, bc)) != SLIM_OK) return bail(s);
+    if (cudaMemset(mv.rec, 0, bc * kBlockVoxels * (uint64_t)m->rs * sizeof(float)) != cudaSuccess ||
+        cudaMemset(mv.blk_mask, 0, bc * sizeof(uint64_t)) != cudaSuccess)
       return bail(cuda_fail(cudaGetLastError(), "cudaMemset"));
   } else {
     const uint64_t rc = (uint64_t)p->voxel_capacity;
@@ -367,8 +370,8 @@ slim_status slim_map_reset(slim_map* m, void* stream) {
   const size_t nh = (size_t)m->n_entries;
   const int tok = prof_begin(m, SLIM_KERNEL_RESET, st);
   if (m->mode != SLIM_OPEN)
-    SLIM_CUDA(launch_zero_used_blocks(m->mv.rec, m->mv.ctr + kCtrBlocks, m->mv.block_cap, m->rs,
-                                      st));
+    SLIM_CUDA(launch_zero_touched_blocks(m->mv.rec, m->mv.blk_mask, m->mv.ctr + kCtrBlocks,
+                                         m->mv.block_cap, m->rs, st));
   else
     SLIM_CUDA(launch_reset_vox_rows(m->mv, st));
   prof_end(m, tok, st);

@@ -61,6 +61,10 @@ struct MapView {
   //   soft (kRecSoftFx): int64 {S, W, c_0 .. c_{K-1}} in units of 2^-32
   //   latest (kRecLatest): {S, W, stamp}
   float* rec;
+  // closed set: per block slot, one bit per 2 x 2 x 2 sub-block whose
+  // records an integration has written since the last reset (the reset
+  // zeroes those records only; the rest of the pool stays zero)
+  uint64_t* blk_mask;
   int32_t rs;
   int32_t K;
   int32_t layout;
@@ -119,6 +123,25 @@ __device__ __forceinline__ void unpack_block(uint64_t k, int32_t& bx, int32_t& b
 
 __device__ __forceinline__ int local_index(int32_t ix, int32_t iy, int32_t iz) {
   return ((ix & 7) * 8 + (iy & 7)) * 8 + (iz & 7);
+}
+
+// The bit of a block's touched mask for the 2 x 2 x 2 sub-block holding
+// local voxel `local` (bits 6-8 x, 3-5 y, 0-2 z).
+__device__ __forceinline__ uint64_t sub_bit(uint32_t local) {
+  return 1ull << ((((local >> 7) & 3u) << 4) | (((local >> 4) & 3u) << 2) | ((local >> 1) & 3u));
+}
+
+// *a |= v (64-bit, no return value).
+__device__ __forceinline__ void red_or_u64(uint64_t* a, uint64_t v) {
+  asm volatile("red.global.or.b64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+
+// Add `bits` to a block's touched mask unless `seen` (an earlier read of the
+// mask) already holds them: bits are only added until the next reset, so a
+// stale read costs at most a redundant reduction, and most writers of a
+// block (hundreds of rays per scan) skip the same-address reduction.
+__device__ __forceinline__ void mark_touched(uint64_t* mask, uint64_t bits, uint64_t seen) {
+  if (bits & ~seen) red_or_u64(mask, bits);
 }
 
 // 64-bit finaliser (splitmix64 style) for bucket selection.

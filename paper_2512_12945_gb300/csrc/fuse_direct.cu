@@ -50,15 +50,24 @@ __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_con
   if (!ray_setup_at(J.g, J.pts, j, ry)) return;
   const uint32_t cls = MODE == 1 ? 0u : argmax_row(J.sem + (size_t)j * J.K, J.K);
   uint32_t slot = kFailSlot;
+  uint64_t bits = 0;  // sub-blocks this ray wrote in the current block
+  uint64_t seen = 0;  // the block's touched mask, read when the ray entered it
   ray_for_each_blk(J.g, ry, [&](int32_t i0, int32_t i1, int32_t i2, float d, bool new_block) {
-    if (new_block) slot = map_block_slot(mv, pack_block(i0 >> 3, i1 >> 3, i2 >> 3));
+    if (new_block) {
+      if (bits) mark_touched(mv.blk_mask + slot, bits, seen);
+      bits = 0;
+      slot = map_block_slot(mv, pack_block(i0 >> 3, i1 >> 3, i2 >> 3));
+      if (slot < mv.block_cap) seen = mv.blk_mask[slot];
+    }
     if (slot >= mv.block_cap) return;
     // the observation adds (w~ d, w~); an observation of weight 0 changes
     // nothing
     const float wt = WT ? obs_weight(J.g, d) : 1.f;
     if (WT && wt == 0.f) return;
     const float wd = WT ? __fmul_rn(wt, d) : d;
-    float* r = mv.rec + ((size_t)slot * kBlockVoxels + local_index(i0, i1, i2)) * mv.rs;
+    const int loc = local_index(i0, i1, i2);
+    bits |= sub_bit(loc);
+    float* r = mv.rec + ((size_t)slot * kBlockVoxels + loc) * mv.rs;
     if (MODE == 0) {
       red_add_v2(r + 2 * cls, wd, wt);
     } else if (MODE == 1) {
@@ -79,6 +88,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_fuse_direct(const __grid_con
       atomicMax(reinterpret_cast<unsigned long long*>(r + 2), stamp);
     }
   });
+  if (bits) mark_touched(mv.blk_mask + slot, bits, seen);
 }
 
 // All jobs of b share one variant: mode (0 one-hot, 1 soft, 2 latest) + 3

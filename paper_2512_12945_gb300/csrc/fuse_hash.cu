@@ -269,8 +269,10 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
     if (slot >= mv.block_cap) continue;  // kFailSlot: a fault was raised for the block
     const uint32_t cnt = kc.y;
     const int32_t qs = (int32_t)vsum[e] - (int32_t)(cnt * kQOne);
-    float* r = mv.rec + ((size_t)slot * kBlockVoxels + ((key >> 6) & 511u)) * mv.rs;
+    const uint32_t loc = (key >> 6) & 511u;
+    float* r = mv.rec + ((size_t)slot * kBlockVoxels + loc) * mv.rs;
     red_add_v2(r + 2 * (key & 63u), __fmul_rn((float)qs, qunit), (float)cnt);
+    mark_touched(mv.blk_mask + slot, sub_bit(loc), mv.blk_mask[slot]);
   }
 
   // 4. pairs the table could not take go to HBM one by one
@@ -290,8 +292,10 @@ __device__ __forceinline__ void fuse_hash_tile(const MapView& mv, const ScanGeom
         raise_status(mv.ctr, kDevInternal, 8);
         return;
       }
-      float* r = mv.rec + ((size_t)slot * kBlockVoxels + local_index(i0, i1, i2)) * mv.rs;
+      const int loc = local_index(i0, i1, i2);
+      float* r = mv.rec + ((size_t)slot * kBlockVoxels + loc) * mv.rs;
       red_add_v2(r + 2 * cls, d, 1.f);
+      mark_touched(mv.blk_mask + slot, sub_bit(loc), mv.blk_mask[slot]);
     });
   }
 }
@@ -360,24 +364,45 @@ cudaError_t hash_setup_attributes() {
   return e;
 }
 
-// Keeps a record pool zero beyond its allocation counter: zeroes the records
-// of blocks [0, min(*nblocks, capacity)) so that a reset map hands out zeroed
-// blocks (a pool is zeroed once when the map is created).
-__global__ void __launch_bounds__(256) k_zero_used_blocks(float4* rec, const uint32_t* nblocks,
-                                                          uint32_t block_cap, int rs) {
+// Keeps a record pool zero outside the sub-blocks integrations write: for
+// each block [0, min(*nblocks, capacity)), zeroes the records of every 2 x 2
+// x 2 sub-block its touched mask names (four runs of two consecutive
+// records: z pairs at the four (x, y) of the sub-block) and clears the mask,
+// so that a reset map hands out zeroed blocks. One warp per block. rs is
+// even for every record layout, so each run starts and ends on a 16-byte
+// boundary.
+__global__ void __launch_bounds__(256) k_zero_touched_blocks(float4* rec, uint64_t* mask,
+                                                             const uint32_t* nblocks,
+                                                             uint32_t block_cap, int rs) {
   const uint32_t nb = min(*(volatile const uint32_t*)nblocks, block_cap);
-  const size_t n4 = (size_t)nb * kBlockVoxels * (size_t)rs / 4;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
-       i += (size_t)gridDim.x * blockDim.x)
-    rec[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const unsigned lane = lane_id();
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int run4 = rs / 2;  // float4 per run of two records
+  for (int64_t blk = gw; blk < (int64_t)nb; blk += nw) {
+    uint64_t m = mask[blk];
+    float4* base = rec + (size_t)blk * kBlockVoxels * (size_t)rs / 4;
+    while (m) {
+      const int sb = __ffsll((long long)m) - 1;
+      m &= m - 1;
+      const int x0 = 2 * (sb >> 4), y0 = 2 * ((sb >> 2) & 3), z0 = 2 * (sb & 3);
+      // 4 runs x run4 float4, spread over the lanes
+      for (int k = (int)lane; k < 4 * run4; k += 32) {
+        const int run = k / run4, off = k - run * run4;
+        const int loc = ((x0 + (run >> 1)) * 8 + (y0 + (run & 1))) * 8 + z0;
+        base[(size_t)loc * rs / 4 + off] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    if (lane == 0) mask[blk] = 0ull;
+  }
 }
 
-cudaError_t launch_zero_used_blocks(float* rec, const uint32_t* nblocks, uint32_t block_cap,
-                                    int rs, cudaStream_t st) {
+cudaError_t launch_zero_touched_blocks(float* rec, uint64_t* mask, const uint32_t* nblocks,
+                                       uint32_t block_cap, int rs, cudaStream_t st) {
   if (!rec) return cudaSuccess;
   const int sms = g_sms > 0 ? g_sms : 152;
-  k_zero_used_blocks<<<(unsigned)(sms * 8), 256, 0, st>>>(reinterpret_cast<float4*>(rec), nblocks,
-                                                       block_cap, rs);
+  k_zero_touched_blocks<<<(unsigned)(sms * 8), 256, 0, st>>>(reinterpret_cast<float4*>(rec),
+                                                             mask, nblocks, block_cap, rs);
   return cudaGetLastError();
 }
 

@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(256, 2)
     const uint32_t slot = act ? tb_slot[key2 >> 9] : kNoSlot;
     float* r = (slot < kFailSlot) ? mv.rec + ((size_t)slot * kBlockVoxels + (key2 & 511u)) * mv.rs
                                   : nullptr;
+    if (r) mark_touched(mv.blk_mask + slot, sub_bit(key2 & 511u), mv.blk_mask[slot]);
     if (MODE == 0) {
       // (voxel, class) groups: sum d per group leader through warp scratch
       const uint32_t cl = cls[pt];

@@ -43,9 +43,10 @@ cudaError_t launch_fuse_direct(const MapView& mv, const ScanGeom& g, const float
                                const float* sem, int64_t n, int K, int latest, int soft,
                                cudaStream_t st);
 cudaError_t launch_direct_batch(HashBatch& b, int mode, cudaStream_t st);
-// Zero the records of blocks [0, *nblocks) of a closed-set record pool.
-cudaError_t launch_zero_used_blocks(float* rec, const uint32_t* nblocks, uint32_t block_cap,
-                                    int rs, cudaStream_t st);
+// Zero the records of the touched sub-blocks of blocks [0, *nblocks) of a
+// closed-set record pool and clear their masks.
+cudaError_t launch_zero_touched_blocks(float* rec, uint64_t* mask, const uint32_t* nblocks,
+                                       uint32_t block_cap, int rs, cudaStream_t st);
 cudaError_t launch_fuse_hash(const MapView& mv, const ScanGeom& g, const float* pts,
                              const float* sem, int64_t n, int K, int tile, int band_blocks,
                              cudaStream_t st);
