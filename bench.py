@@ -5,8 +5,8 @@ Workload: the urban LiDAR sequence — 100 scans of 64 beams x 2048 azimuths
 (131,072 points per scan, ~120k valid, ranges 1-80 m) ray-cast in a seeded
 synthetic street, 0.1 m voxels, 0.3 m truncation, 20 classes (closed-set
 one-hot Dirichlet counts). One step = empty the map (slim_map_reset) and
-integrate all 100 scans with one slim_integrate_batch call (16 scans per
-launch of the autotuned strategy) with inputs resident in HBM (1.2 GB per
+integrate all 100 scans with one slim_integrate_batch call (up to 64 scans
+per launch of the autotuned strategy) with inputs resident in HBM (1.2 GB per
 step, larger than L2, so every step streams from HBM).
 
 Prints one JSON line. Extra keys: roofline (dominant kernel, algorithmic
@@ -211,10 +211,10 @@ def algorithmic_bytes(counts, n_scans, K=K_CLASSES):
 
 
 STRATEGY = {0: ("k_fuse_direct", "fuse_direct.cu",
-                 "slim_integrate_batch: 16 scans per grid, direct per-pair red.add into "
+                 "slim_integrate_batch: up to 64 scans per grid, direct per-pair red.add into "
                  "L2-resident records")}
 HASH_STRATEGY = ("k_fuse_hash_persistent", "fuse_hash.cu",
-                 "slim_integrate_batch: 16 scans per persistent launch, shared-memory "
+                 "slim_integrate_batch: up to 64 scans per persistent launch, shared-memory "
                  "(voxel, class) hash tiles of {} points")
 
 
@@ -334,7 +334,7 @@ def run_ours(args):
                ctypes.c_void_p(se.data_ptr())) for p, se, po in zip(pts, sem, poses)]
     stream = torch.cuda.current_stream()
     sp = ctypes.c_void_p(stream.cuda_stream)
-    # the whole 100-scan sequence as one batch (16 scans per persistent launch)
+    # the whole 100-scan sequence as one batch (up to 64 scans per launch)
     items = (slim.slim_batch_item * len(args_c))()
     for k, (a, po) in enumerate(zip(args_c, poses)):
         items[k].map = h
@@ -537,10 +537,10 @@ def run_ours(args):
     # both closed one-hot strategies per scan and batched
     paths = {"sort": ("sort", 0, "slim_integrate per scan, CTA radix sort + segmented reduction"),
              "direct": ("direct", 0, "slim_integrate per scan, direct per-pair red.add"),
-             "direct_batch": ("direct", 0, "slim_integrate_batch, 16 scans per grid, direct "
+             "direct_batch": ("direct", 0, "slim_integrate_batch, up to 64 scans per grid, direct "
                                            "per-pair red.add"),
              "hash": ("hash", 256, "slim_integrate per scan, shared-memory hash tiles of 256"),
-             "hash_batch": ("hash", 256, "slim_integrate_batch, 16 scans per persistent launch, "
+             "hash_batch": ("hash", 256, "slim_integrate_batch, up to 64 scans per persistent launch, "
                                          "shared-memory hash tiles of 256")}
     for var in (() if args.no_variants else ("sort", "direct", "direct_batch", "hash",
                                               "hash_batch")):

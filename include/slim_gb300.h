@@ -360,8 +360,8 @@ typedef struct {
 
 /* Integrate n_items scans, possibly of different maps and sizes, in few
  * launches: closed-set items of maps with direct reductions share one grid
- * per mode and weighting and per 16 items (one CTA per 256 points of each
- * item); items of hash-tile maps share one persistent launch per 16 items
+ * per mode and weighting and per 64 items (one CTA per 256 points of each
+ * item); items of hash-tile maps share one persistent launch per 64 items
  * (CTAs take tiles of all items from a device counter); open-set items
  * share one tile grid per embedding storage and 16 items (one CTA per pixel
  * tile of each item) and one update launch per storage and 16 maps;

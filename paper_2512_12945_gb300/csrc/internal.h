@@ -29,7 +29,7 @@ struct HashJob {
   int32_t tile_points;  // set by launch_hash_batch
   uint32_t tile_begin;  // set by launch_hash_batch
 };
-constexpr int kMaxHashJobs = 16;
+constexpr int kMaxHashJobs = 64;  // 312 B each: ~20 KB of kernel parameters
 struct HashBatch {
   HashJob job[kMaxHashJobs];
   int32_t n_jobs;
