@@ -363,8 +363,8 @@ typedef struct {
  * per mode and weighting and per 64 items (one CTA per 256 points of each
  * item); items of hash-tile maps share one persistent launch per 64 items
  * (CTAs take tiles of all items from a device counter); open-set items
- * share one tile grid per embedding storage and 16 items (one CTA per pixel
- * tile of each item) and one update launch per storage and 16 maps;
+ * share one tile grid per embedding storage and 48 items (one CTA per pixel
+ * tile of each item) and one update launch per storage and 48 maps;
  * sort-aggregation items are integrated one by one by their own kernels.
  * Items of the same map are fused as one observation set (Theorems 1-2 make
  * the result independent of order and grouping; the latest-label mode keeps

@@ -860,7 +860,7 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
     b.n_jobs = 0;
     return e == cudaSuccess ? SLIM_OK : cuda_fail(e, "launch_hash_batch");
   };
-  // direct-reduction maps share one grid per 16 scans, mode and weighting
+  // direct-reduction maps share one grid per 64 scans, mode and weighting
   HashBatch nb[6];
   slim_map* direct0[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   for (int q = 0; q < 6; ++q) nb[q].n_jobs = 0;

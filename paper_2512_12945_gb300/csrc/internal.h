@@ -83,7 +83,7 @@ struct OpenJob {  // 64-byte aligned by its tensor map
   uint32_t tiles_x;     // set by launch_open_tiles
   uint32_t tile_begin;  // set by launch_open_tiles
 };
-constexpr int kMaxOpenJobs = 16;
+constexpr int kMaxOpenJobs = 48;  // 512 B each: ~24 KB of kernel parameters
 struct OpenBatch {
   OpenJob job[kMaxOpenJobs];
   int32_t n_jobs;

@@ -925,8 +925,8 @@ slim_status open_integrate(slim_map* m, const ScanGeom& g, const float* pts, con
   return SLIM_OK;
 }
 
-// Open-set items of a batch: one tile launch per storage kind and 16 items,
-// then one apply launch per storage kind and 16 maps. Items of the same map
+// Open-set items of a batch: one tile launch per storage kind and 48 items,
+// then one apply launch per storage kind and 48 maps. Items of the same map
 // share the map's accumulators (one observation set).
 slim_status open_integrate_batch(const std::vector<OpenItem>& items, cudaStream_t st) {
   if (items.empty()) return SLIM_OK;
