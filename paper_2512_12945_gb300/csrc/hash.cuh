@@ -20,7 +20,8 @@ __device__ __forceinline__ uint32_t hash_find(const MapView& mv, uint64_t key) {
   uint32_t h = entry_of(mv, key);
   for (int pr = 0; pr < mv.max_probe; ++pr) {
     const uint64_t cur = mv.hkeys[h];
-    if (cur == key) return mv.hvals[h];
+    const uint32_t v = mv.hvals[h];  // loaded with the key: one round trip
+    if (cur == key) return v;
     if (cur == kEmptyKey) return kNoSlot;
     h = (h + 1) & mv.entry_mask;
   }
@@ -57,6 +58,10 @@ __device__ __forceinline__ uint32_t map_block_slot(const MapView& mv, uint64_t k
   uint32_t h = entry_of(mv, key);
   for (int pr = 0; pr < mv.max_probe; ++pr) {
     const uint64_t cur = *(volatile uint64_t*)&mv.hkeys[h];
+    // the slot is loaded together with the key, so that finding a published
+    // block costs one round trip; read before the key, it can only be older
+    // (kNoSlot, then re-read below while unpublished)
+    const uint32_t vpre = ld_relaxed(&mv.hvals[h]);
     bool mine = false, found = cur == key;
     if (!found && cur == kEmptyKey) {
       const unsigned long long prev = atomicCAS((unsigned long long*)&mv.hkeys[h],
@@ -78,7 +83,7 @@ __device__ __forceinline__ uint32_t map_block_slot(const MapView& mv, uint64_t k
       return v;
     }
     if (found) {
-      uint32_t v = ld_relaxed(&mv.hvals[h]);
+      uint32_t v = vpre;
       if (v == kNoSlot) {
         const uint64_t t0 = global_ns();
         while ((v = ld_relaxed(&mv.hvals[h])) == kNoSlot) {
