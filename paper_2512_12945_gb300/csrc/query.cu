@@ -115,36 +115,44 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // Online softmax over one chunk of W accumulator columns [c0, c0 + W) of a
-// row: x = acc * colscale[c] * rowscale are base-2 logits (cos / T times
+// row: acc * colscale[c] * rowscale are base-2 logits (cos / T times
 // log2 e); columns >= Q are ignored. The chunk's maximum (with the lowest
-// index among ties) is found by a tree, then its W exponentials are
-// independent, so the chain per chunk is short.
+// index among ties) is found by a tree on acc * colscale[c] (the row scale
+// is positive), then its W exponentials are independent, so the chain per
+// chunk is short.
 template <int W>
 __device__ __forceinline__ void softmax_chunk(const uint32_t (&r)[W], int c0, int Q,
                                               const float* colscale, float rowscale, float* scores,
                                               float cosscale, float& mrun, float& srun, int& best) {
-  float x[W];
-  int ix[W];
+  // y = acc |q|^-1 log2(e) / T: the row's base-2 logits divided by its
+  // positive row scale |m|^-1, so y orders the columns as the logits do; the
+  // row scale enters once, in the exponent's FMA
+  float y[W];
   const float4* cs4 = reinterpret_cast<const float4*>(colscale + c0);  // c0 % 16 == 0
 #pragma unroll
   for (int j4 = 0; j4 < W / 4; ++j4) {
     const float4 cv = cs4[j4];
-    const float cj[4] = {cv.x, cv.y, cv.z, cv.w};
+    y[4 * j4 + 0] = __uint_as_float(r[4 * j4 + 0]) * cv.x;
+    y[4 * j4 + 1] = __uint_as_float(r[4 * j4 + 1]) * cv.y;
+    y[4 * j4 + 2] = __uint_as_float(r[4 * j4 + 2]) * cv.z;
+    y[4 * j4 + 3] = __uint_as_float(r[4 * j4 + 3]) * cv.w;
+  }
+  if (c0 + W > Q) {  // the chunk holds padding columns (uniform over the warp)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = 4 * j4 + u, c = c0 + j;
-      const float acc = __uint_as_float(r[j]);
-      x[j] = c < Q ? acc * cj[u] * rowscale : -INFINITY;
-      ix[j] = c;
-      if (scores && c < Q) scores[c] = acc * cj[u] * cosscale;
-    }
+    for (int j = 0; j < W; ++j)
+      if (c0 + j >= Q) y[j] = -INFINITY;
+  }
+  if (scores) {
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if (c0 + j < Q) scores[c0 + j] = y[j] * cosscale;
   }
   float mx[W];
   int bi[W];
 #pragma unroll
   for (int j = 0; j < W; ++j) {
-    mx[j] = x[j];
-    bi[j] = ix[j];
+    mx[j] = y[j];
+    bi[j] = c0 + j;
   }
 #pragma unroll
   for (int w = W / 2; w > 0; w >>= 1) {
@@ -155,11 +163,12 @@ __device__ __forceinline__ void softmax_chunk(const uint32_t (&r)[W], int c0, in
       mx[j] = take ? mx[j + w] : mx[j];
     }
   }
-  const float mnew = fmaxf(mrun, mx[0]);
-  if (mx[0] > mrun) best = bi[0];
+  const float mc = mx[0] * rowscale;
+  const float mnew = fmaxf(mrun, mc);
+  if (mc > mrun) best = bi[0];
   float e[W];
 #pragma unroll
-  for (int j = 0; j < W; ++j) e[j] = ex2_approx(x[j] - mnew);
+  for (int j = 0; j < W; ++j) e[j] = ex2_approx(__fmaf_rn(y[j], rowscale, -mnew));
 #pragma unroll
   for (int w = W / 2; w > 0; w >>= 1) {
 #pragma unroll
