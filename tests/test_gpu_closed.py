@@ -298,3 +298,23 @@ def test_soft_counts_full_scans(K, agg):
         m.sync()
         compare_closed(to_np(m.extract()), o, "soft")
 
+
+
+@pytest.mark.parametrize("mode,agg", [("onehot", "direct"), ("onehot", "hash"), ("onehot", "sort"),
+                                      ("soft", "direct"), ("soft", "sort"), ("latest", "auto")])
+def test_reset_leaves_no_stale_records(mode, agg):
+    """The reset zeroes only the 2 x 2 x 2 sub-blocks each block marked as
+    written. Integrate two scans, reset, integrate two other scans: the map
+    must be the oracle's map of the second pair alone, for every record
+    writer (direct reductions, hash tiles, sort tiles) and record layout."""
+    import copy
+    w = synth.street_lidar(n_scans=4, n_az=512)
+    m = gpu_map(w, mode=mode, scans=w.scans[:2], aggregation=agg)
+    m.reset()
+    for s in w.scans[2:]:
+        m.integrate(torch.from_numpy(s["pts"]).cuda(), s["pose"], torch.from_numpy(s["sem"]).cuda())
+    m.sync()
+    w2 = copy.copy(w)
+    w2.scans = w.scans[2:]
+    o = oracle_map(w2, mode=mode).extract()
+    compare_closed(to_np(m.extract()), o, "soft" if mode == "soft" else "onehot")
