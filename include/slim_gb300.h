@@ -174,9 +174,11 @@ slim_status slim_map_destroy(slim_map* m);
 
 /* Empty the map (all blocks and voxels gone, status cleared), keeping its
  * memory. Queued on `stream`. For closed-set maps it also re-zeroes the
- * records of the blocks allocated so far (one kernel, SLIM_KERNEL_RESET):
- * the record pool is kept zero beyond the allocation counter, so
- * integration never zeroes a block it creates. */
+ * records the integrations since the last reset wrote (one kernel,
+ * SLIM_KERNEL_RESET):
+ * the record pool is kept zero outside the 2 x 2 x 2 sub-blocks written since
+ * the last reset (every block marks them), so integration never zeroes a
+ * block it creates. */
 slim_status slim_map_reset(slim_map* m, void* stream);
 
 /* Integrate one scan (Sec. III-A to III-D). For each of the n points:
@@ -191,9 +193,13 @@ slim_status slim_map_reset(slim_map* m, void* stream);
  *   min(d, tau) and the point's semantics:
  *     closed modes: sem_dev = n x K float32 class probabilities (row-major);
  *     SLIM_OPEN:    sem_dev = n x l float32 embeddings (row-major, 16-byte
- *                   aligned).
+ *                   aligned), every element within embed_bound in
+ *                   magnitude (otherwise the observations that carry it
+ *                   are not fused and the map's status becomes
+ *                   SLIM_ERR_RANGE).
  * Fusion: W += 1, D running average (w~ = 1), then the mode's update.
- * n may be 0. n <= max_points. Asynchronous on `stream`. */
+ * n may be 0. n <= max_points; SLIM_OPEN: n <= 2^23 (SLIM_ERR_ARG beyond).
+ * Asynchronous on `stream`. */
 slim_status slim_integrate(slim_map* m, const float* pts_dev, int64_t n,
                            const double pose_host[16], const void* sem_dev,
                            void* stream);
