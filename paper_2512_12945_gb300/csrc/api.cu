@@ -1,6 +1,7 @@
 // C ABI of the scan-integration library (declared in include/slim_gb300.h).
 // Host side only: argument checks, FP64 pose composition, device memory of
 // each map, and the launch sequence of every entry point.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -840,6 +841,23 @@ slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, 
     if ((reinterpret_cast<uintptr_t>(it.pts_dev) & 3) ||
         (reinterpret_cast<uintptr_t>(it.sem_dev) & (m->mode == SLIM_OPEN ? 15 : 3)))
       return fail(SLIM_ERR_ARG, "item " + std::to_string(k) + ": misaligned pts/sem");
+  }
+  {  // open-set maps: at most 2^23 points per map and call (checked before
+     // anything is queued)
+    std::vector<std::pair<const slim_map*, int64_t>> per_map;
+    for (int32_t k = 0; k < n_items; ++k) {
+      if (items[k].map->mode != SLIM_OPEN) continue;
+      auto f = std::find_if(per_map.begin(), per_map.end(),
+                            [&](const std::pair<const slim_map*, int64_t>& e) {
+                              return e.first == items[k].map;
+                            });
+      if (f == per_map.end()) {
+        per_map.emplace_back(items[k].map, 0);
+        f = per_map.end() - 1;
+      }
+      if ((f->second += items[k].n) > ((int64_t)1 << 23))
+        return fail(SLIM_ERR_ARG, "open set: at most 2^23 points per map and call");
+    }
   }
   cudaStream_t st = (cudaStream_t)stream;
   // closed one-hot scans with hash aggregation share persistent launches
