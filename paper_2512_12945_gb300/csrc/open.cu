@@ -13,17 +13,18 @@
 // observations add up to the same update (Theorem 2 is stated for sets).
 //
 // Pipeline per integration call (pairs never reach HBM):
-//   k_open_tile   one CTA per tile of 16 x 16 pixels of an organized frame
-//                 (or 256 consecutive points): band DDA per pixel; the tile's
-//                 distinct voxels in a shared-memory table with a pixel mask,
-//                 count and fixed-point sum of d per voxel; blocks and voxel
+//   k_open_tile   one CTA per tile of 256 pixels of an organized frame
+//                 (16 x 16, 8 x 32 or 32 x 8) or 256 consecutive points: band
+//                 DDA per pixel; the tile's distinct voxels in a shared-memory
+//                 table with their pixel lists and sums of d; blocks and voxel
 //                 rows looked up or created in the map (a new row gets its
 //                 shift, the embedding of one of its pixels, before it is
 //                 published); the embedding rows streamed in 64-element
 //                 chunks by TMA into shared memory, each read once from HBM;
-//                 per (voxel, chunk) one warp sums y = z - s and y^2 over the
-//                 voxel's pixels (packed FP32x2 arithmetic) and adds them to
-//                 the row's accumulator with one vector reduction per lane.
+//                 per chunk a warp takes four pieces (at most 64 pixels of a
+//                 voxel's list each), sums y = z - s and y^2 over their
+//                 pixels (packed FP32x2 arithmetic) and adds them to the
+//                 rows' accumulators as exact 64-bit integer reductions.
 //   k_open_apply  one warp per row the call touched: the update above from
 //                 the accumulator, the row's state read and written once,
 //                 the accumulator cleared.
@@ -141,16 +142,6 @@ __device__ __forceinline__ uint64_t evict_first_policy() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
-}
-
-template <int BF16>
-__device__ __forceinline__ float2 load2(const void* base, size_t idx) {
-  if (BF16) {
-    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(
-        static_cast<const __nv_bfloat16*>(base) + idx);
-    return __bfloat1622float2(v);
-  }
-  return *reinterpret_cast<const float2*>(static_cast<const float*>(base) + idx);
 }
 
 template <int BF16>
