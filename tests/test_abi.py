@@ -64,3 +64,29 @@ def test_null_handles_rejected(L):
     assert L.slim_extract_tsdf(None, None, None, None, None, None, None, 0, ctypes.byref(n), 0,
                                None) == 1
     assert L.slim_map_params_default(None) == 1
+
+
+def test_params_struct_size_matches_the_binding(L):
+    """slim_map_params_default clears the C struct with its own sizeof and
+    sets embed_bound (the last field) to 1: with a sentinel-filled buffer
+    larger than the binding's struct, it must write exactly the binding's
+    size, so the two layouts agree."""
+    n = ctypes.sizeof(slim.slim_map_params)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    assert L.slim_map_params_default(ctypes.cast(buf, ctypes.POINTER(slim.slim_map_params))) == 0
+    assert all(b == 0xAB for b in bytes(buf)[n:]), "C struct larger than the binding's"
+    p = slim.slim_map_params.from_buffer(buf)
+    assert p.embed_bound == 1.0 and p.voxel_size == pytest.approx(0.1)
+
+
+def test_open_set_embed_bound_range_checked(L):
+    """embed_bound must lie in [2^-16, 2^16] for open-set maps (checked on
+    the host, nothing allocated)."""
+    for b in (0.0, -1.0, 2.0 ** 17):
+        q = slim.slim_map_params_default()
+        q.mode = 2
+        q.embed_dim = 64
+        q.embed_bound = b
+        h = ctypes.c_void_p()
+        assert L.slim_map_create(ctypes.byref(q), ctypes.byref(h)) == 1
+        assert b"embed_bound" in L.slim_last_error()
