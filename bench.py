@@ -797,8 +797,8 @@ def run_adjoint(args):
         D, W, c, ijk = autograd.integrate(m, poses, pts, sem)
         state["out"] = (D, c)
 
-    def fwd_bwd():
-        D, W, c, ijk = autograd.integrate(m, poses, pts, sem)
+    def fwd_bwd(stored=False):
+        D, W, c, ijk = autograd.integrate(m, poses, pts, sem, stored=stored)
         n = D.shape[0]
         if "sel" not in state or state["n"] != n:
             state["n"] = n
@@ -828,20 +828,49 @@ def run_adjoint(args):
         fwd_by[agg] = _timed(integ, args.steps, args.warmup, stream)
         mv.close()
     fms = _timed(fwd, args.steps, args.warmup, stream)
-    torch.cuda.reset_peak_memory_stats()
-    base = torch.cuda.memory_allocated()
     tms = _timed(fwd_bwd, args.steps, args.warmup, stream)
-    peak = torch.cuda.max_memory_allocated() - base
+    # the stored form: the forward keeps each scan's pair list (CSR by point,
+    # 4 B per pair and per point), the backward reads it
+    sms_ = _timed(lambda: fwd_bwd(stored=True), args.steps, args.warmup, stream)
+    fwd()
+    rec_ms = _timed(lambda: [m.record_pairs(p.detach(), po) for p, po in zip(pts, poses)],
+                    args.steps, 1, stream)
+    lists = [m.record_pairs(p.detach(), po) for p, po in zip(pts, poses)]
+    list_bytes = sum(4 * (o.numel() + v.numel()) for o, v in lists)
+    list_pairs = sum(v.numel() for _, v in lists)
+    del lists
+
+    def peak_of(stored):
+        """Device memory the forward + backward allocates above the inputs,
+        from the same clean state for both forms (no gradients, no outputs
+        held, allocator cache emptied)."""
+        for t in pts + sem:
+            t.grad = None
+        state.pop("out", None)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        fwd_bwd(stored=stored)
+        torch.cuda.synchronize()
+        return torch.cuda.max_memory_allocated() - base
+
+    peak = peak_of(False)
+    peak_s = peak_of(True)
     valid = sum(int((np.linalg.norm(s["pts"], axis=1) >= w.min_range).sum()) for s in w.scans)
-    # recompute vs stored: a reverse pass that kept its (voxel, point) pairs
-    # would hold 16 B per pair (64-bit voxel key, point index, FP32 SDF);
-    # the pair counts are the oracle's, per scan
+    # recompute vs stored, both measured; the oracle's pair count beside them
     mem = {"saved_for_backward": "inputs only; (voxel, point) pairs recomputed",
-           "torch_peak_bytes_above_inputs": int(peak)}
+           "torch_peak_bytes_above_inputs": int(peak),
+           "stored": {"saved_for_backward": "inputs + each scan's pair list (slim_record_pairs: "
+                                            "CSR offsets and a uint32 voxel index per pair)",
+                      "pair_list_bytes": int(list_bytes), "pairs": int(list_pairs),
+                      "torch_peak_bytes_above_inputs": int(peak_s),
+                      "forward_backward_ms": sms_, "record_pairs_ms": rec_ms,
+                      "backward_ms": sms_ - fms - rec_ms}}
     try:
         with open(ADJOINT_COUNTS) as f:
             pairs = sum(r["pairs"] for r in json.load(f)["scans"])
-        mem.update({"pairs": pairs, "stored_pair_list_bytes": 16 * pairs})
+        mem.update({"oracle_pairs": pairs})
     except (OSError, KeyError, ValueError):
         pass
     line = {"metric": "differentiable integration: points/s forward, forward+backward",

@@ -355,6 +355,31 @@ slim_status slim_backward(slim_map* m, const float* pts_dev, int64_t n,
                           const float* gD_dev, const float* gS_dev, const float* gB_dev,
                           float* gsem_dev, float* gxyz_dev, void* stream);
 
+/* The stored-pair form of the reverse mode (closed set, one-hot and soft
+ * counts): no counterpart in the paper, which has no reverse mode; it is the
+ * alternative slim_backward avoids, kept to measure what storing the pairs
+ * costs. slim_record_pairs writes, for one scan of a map that already holds
+ * it (call after the forward integration, before the next reset), the
+ * scan's (voxel, point) observations in point order and, within a point, in
+ * ray order: offsets_dev (n + 1 uint32, caller-owned device memory)
+ * receives the CSR offsets, vox_dev (cap uint32) each pair's voxel index
+ * (slot * 512 + local, as index_dev of slim_extract_tsdf), *n_pairs the
+ * total. cap = 0 is a size query (offsets_dev is still written); cap below
+ * the total returns SLIM_ERR_CAPACITY. The first call allocates a count
+ * buffer of max_points entries; the call synchronises `stream`.
+ * slim_backward_pairs then gives the results of slim_backward for the same
+ * scan (the same terms in the same order) from the stored list instead of
+ * recomputing the band walk and the hash lookups. Latest-label maps and
+ * weighted maps return SLIM_ERR_UNSUPPORTED. */
+slim_status slim_record_pairs(slim_map* m, const float* pts_dev, int64_t n,
+                              const double pose_host[16], uint32_t* offsets_dev,
+                              uint32_t* vox_dev, int64_t cap, int64_t* n_pairs, void* stream);
+slim_status slim_backward_pairs(slim_map* m, const float* pts_dev, int64_t n,
+                                const double pose_host[16], const uint32_t* offsets_dev,
+                                const uint32_t* vox_dev, const float* gD_dev,
+                                const float* gS_dev, float* gsem_dev, float* gxyz_dev,
+                                void* stream);
+
 /* One work item of a batched integration: a scan for one map. */
 typedef struct {
   slim_map* map;

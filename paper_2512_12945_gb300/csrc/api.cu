@@ -326,12 +326,12 @@ slim_status slim_map_create(const slim_map_params* p, slim_map** out) {
   unsigned char* tmp = nullptr;
   if ((s = m->alloc(&tmp, radix_sort_temp_bytes((int64_t)bc))) != SLIM_OK) return bail(s);
   m->ex_tmp = tmp;
-  if (cudaMallocHost(&m->pinned, kNumCounters * sizeof(uint32_t)) != cudaSuccess) {
+  if (cudaMallocHost(&m->pinned, kPinnedWords * sizeof(uint32_t)) != cudaSuccess) {
     cudaGetLastError();
     m->pinned = nullptr;
     return bail(fail(SLIM_ERR_NOMEM, "cudaMallocHost failed"));
   }
-  std::memset(m->pinned, 0, kNumCounters * sizeof(uint32_t));
+  std::memset(m->pinned, 0, kPinnedWords * sizeof(uint32_t));
   if (cudaMemset(mv.ctr, 0, kNumCounters * sizeof(uint32_t)) != cudaSuccess)
     return bail(cuda_fail(cudaGetLastError(), "cudaMemset"));
   cudaError_t e = cudaSuccess;
@@ -824,6 +824,53 @@ slim_status slim_backward(slim_map* m, const float* pts_dev, int64_t n,
   return run_backward(m, g, pts_dev, static_cast<const float*>(sem_dev), n, gD_dev, gS_dev,
                       m->mode == SLIM_OPEN ? gB_dev : nullptr, gsem_dev, gxyz_dev,
                       (cudaStream_t)stream);
+}
+
+// Arguments shared by the stored-pair calls; returns SLIM_OK or the failure.
+static slim_status check_pair_call(slim_map* m, const float* pts_dev, int64_t n,
+                                   const double* pose_host) {
+  if (!m) return fail(SLIM_ERR_ARG, "map is NULL");
+  if (n < 0 || n > m->p.max_points) return fail(SLIM_ERR_ARG, "n must be in [0, max_points]");
+  if (!pose_host || !finite_pose(pose_host)) return fail(SLIM_ERR_ARG, "pose missing or not finite");
+  if (n > 0 && !pts_dev) return fail(SLIM_ERR_ARG, "pts is NULL with n > 0");
+  if (m->mode != SLIM_CLOSED_ONEHOT && m->mode != SLIM_CLOSED_SOFT)
+    return fail(SLIM_ERR_UNSUPPORTED, "stored pair lists serve the one-hot and soft modes");
+  if (m->p.weighting != SLIM_WEIGHT_CONSTANT)
+    return fail(SLIM_ERR_UNSUPPORTED, "the adjoint is for maps with w~ = 1");
+  return SLIM_OK;
+}
+
+slim_status slim_record_pairs(slim_map* m, const float* pts_dev, int64_t n,
+                              const double pose_host[16], uint32_t* offsets_dev,
+                              uint32_t* vox_dev, int64_t cap, int64_t* n_pairs, void* stream) {
+  slim_status s = check_pair_call(m, pts_dev, n, pose_host);
+  if (s != SLIM_OK) return s;
+  if (!offsets_dev || !n_pairs) return fail(SLIM_ERR_ARG, "offsets and n_pairs are required");
+  if (cap < 0) return fail(SLIM_ERR_ARG, "cap must be >= 0");
+  if (cap > 0 && !vox_dev) return fail(SLIM_ERR_ARG, "vox is NULL with cap > 0");
+  ScanGeom g;
+  compose_pose(pose_host, m->p.body_from_sensor, g, m->p.voxel_size, m->p.trunc,
+               m->p.min_range, m->p.max_range, m->cap, m->p.weighting, m->p.weight_eps);
+  return run_record_pairs(m, g, pts_dev, n, offsets_dev, vox_dev, cap, n_pairs,
+                          (cudaStream_t)stream);
+}
+
+slim_status slim_backward_pairs(slim_map* m, const float* pts_dev, int64_t n,
+                                const double pose_host[16], const uint32_t* offsets_dev,
+                                const uint32_t* vox_dev, const float* gD_dev,
+                                const float* gS_dev, float* gsem_dev, float* gxyz_dev,
+                                void* stream) {
+  slim_status s = check_pair_call(m, pts_dev, n, pose_host);
+  if (s != SLIM_OK) return s;
+  if (n > 0 && (!offsets_dev || !vox_dev || !gD_dev || !gsem_dev || !gxyz_dev))
+    return fail(SLIM_ERR_ARG, "offsets, vox, gD, gsem and gxyz are required");
+  if (n > 0 && m->mode == SLIM_CLOSED_SOFT && !gS_dev)
+    return fail(SLIM_ERR_ARG, "gS is required in the soft mode");
+  ScanGeom g;
+  compose_pose(pose_host, m->p.body_from_sensor, g, m->p.voxel_size, m->p.trunc,
+               m->p.min_range, m->p.max_range, m->cap, m->p.weighting, m->p.weight_eps);
+  return run_backward_pairs(m, g, pts_dev, n, offsets_dev, vox_dev, gD_dev, gS_dev, gsem_dev,
+                            gxyz_dev, (cudaStream_t)stream);
 }
 
 slim_status slim_integrate_batch(const slim_batch_item* items, int32_t n_items, void* stream) {

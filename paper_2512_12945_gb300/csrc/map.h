@@ -7,6 +7,9 @@
 #include "internal.h"
 
 namespace slim {
+// Words of a map's pinned host block: the device counters and, at
+// kNumCounters, the pair total read back by slim_record_pairs.
+constexpr int kPinnedWords = kNumCounters + 8;
 // Record a failure message for slim_last_error() and return s.
 slim_status fail(slim_status s, const std::string& msg);
 
@@ -53,7 +56,10 @@ struct slim_map {
   uint32_t* ex_counts = nullptr;
   uint32_t* ex_offs = nullptr;
   void* ex_tmp = nullptr;
-  uint32_t* pinned = nullptr;  // host copy of the device counters
+  uint32_t* pinned = nullptr;  // host copy of the device counters, then spare words
+  // slim_record_pairs scratch (allocated by its first call)
+  uint32_t* pr_counts = nullptr;  // [max_points] pairs per point
+  uint32_t* pr_tmp = nullptr;     // scan partials
   slim::OpenScratch open{};
   slim::QueryScratch qscratch{};
   // kernel timing (slim_profile_enable)
@@ -115,6 +121,12 @@ slim_status run_render(slim_map* m, const double world_from_camera[16], float fx
 slim_status run_backward(slim_map* m, const ScanGeom& g, const float* pts, const float* sem,
                          int64_t n, const float* gD, const float* gS, const float* gB,
                          float* gsem, float* gxyz, cudaStream_t st);
+slim_status run_record_pairs(slim_map* m, const ScanGeom& g, const float* pts, int64_t n,
+                             uint32_t* offsets, uint32_t* vox, int64_t cap, int64_t* n_pairs,
+                             cudaStream_t st);
+slim_status run_backward_pairs(slim_map* m, const ScanGeom& g, const float* pts, int64_t n,
+                               const uint32_t* offsets, const uint32_t* vox, const float* gD,
+                               const float* gS, float* gsem, float* gxyz, cudaStream_t st);
 slim_status run_query(slim_map* m, const uint16_t* q_dev, int32_t Q, float temperature, float tp,
                       int32_t* label, float* prob, float* scores, uint32_t n_rows,
                       cudaStream_t st);

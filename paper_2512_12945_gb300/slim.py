@@ -64,7 +64,8 @@ EXPORTS = ["slim_map_params_default", "slim_map_create", "slim_map_destroy", "sl
            "slim_integrate", "slim_integrate_host", "slim_map_sync", "slim_map_stats",
            "slim_extract_tsdf", "slim_query", "slim_backward", "slim_integrate_batch",
            "slim_profile_enable", "slim_profile_read", "slim_autotune", "slim_query_rows_static",
-           "slim_extract_uncertainty", "slim_render", "slim_integrate_depth", "slim_last_error"]
+           "slim_extract_uncertainty", "slim_render", "slim_integrate_depth", "slim_record_pairs",
+           "slim_backward_pairs", "slim_last_error"]
 KERNELS = ["traverse", "fuse_closed", "open_tile", "open_apply", "query", "backward", "batch",
            "reset", "render"]
 N_KINDS = 16
@@ -109,6 +110,8 @@ def lib():
             "slim_extract_uncertainty": [P, P, I64, ctypes.POINTER(I64), P],
             "slim_render": [P, P, F, F, F, F, I32, I32, F, F, P, P, P, P, P, P],
             "slim_integrate_depth": [P, P, I32, I32, F, F, F, F, P, P, P],
+            "slim_record_pairs": [P, P, I64, P, P, P, I64, ctypes.POINTER(I64), P],
+            "slim_backward_pairs": [P, P, I64, P, P, P, P, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -330,6 +333,41 @@ def slim_backward(h, pts, pose, sem, gD, gS, gB, width, stream=None):
     return gsem, gxyz
 
 
+def slim_record_pairs(h, pts, pose, stream=None):
+    """The stored pair list of one scan of the map: (offsets int32 [n + 1],
+    voxel indices int32 [pairs]), CSR by point (size query, then the list)."""
+    n = pts.shape[0]
+    dev = pts.device
+    offsets = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    keep, p_pose = _pose_arr(pose)
+    pp = _dev_ptr(pts, torch.float32, "pts", (n, 3))
+    total = ctypes.c_int64(0)
+    _check(lib().slim_record_pairs(h, pp, n, p_pose, ctypes.c_void_p(offsets.data_ptr()), None, 0,
+                                   ctypes.byref(total), _stream(stream)), "slim_record_pairs")
+    vox = torch.empty(max(total.value, 1), dtype=torch.int32, device=dev)
+    _check(lib().slim_record_pairs(h, pp, n, p_pose, ctypes.c_void_p(offsets.data_ptr()),
+                                   ctypes.c_void_p(vox.data_ptr()), vox.numel(),
+                                   ctypes.byref(total), _stream(stream)), "slim_record_pairs")
+    return offsets, vox[:total.value]
+
+
+def slim_backward_pairs(h, pts, pose, offsets, vox, gD, gS, width, stream=None):
+    n = pts.shape[0]
+    dev = pts.device
+    gsem = torch.empty((n, width), dtype=torch.float32, device=dev)
+    gxyz = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    keep, p_pose = _pose_arr(pose)
+    _check(lib().slim_backward_pairs(h, _dev_ptr(pts, torch.float32, "pts", (n, 3)), n, p_pose,
+                                     _dev_ptr(offsets, torch.int32, "offsets", (n + 1,)),
+                                     ctypes.c_void_p(vox.data_ptr()),
+                                     _dev_ptr(gD, torch.float32, "gD"),
+                                     _dev_ptr(gS, torch.float32, "gS"),
+                                     ctypes.c_void_p(gsem.data_ptr()),
+                                     ctypes.c_void_p(gxyz.data_ptr()), _stream(stream)),
+           "slim_backward_pairs")
+    return gsem, gxyz
+
+
 def slim_profile_enable(h, on):
     _check(lib().slim_profile_enable(h, int(bool(on))), "slim_profile_enable")
 
@@ -454,3 +492,10 @@ class Map:
 
     def backward(self, pts, pose, sem, gD, gS, gB=None, stream=None):
         return slim_backward(self.handle, pts, pose, sem, gD, gS, gB, self.width, stream)
+
+    def record_pairs(self, pts, pose, stream=None):
+        return slim_record_pairs(self.handle, pts, pose, stream)
+
+    def backward_pairs(self, pts, pose, offsets, vox, gD, gS, stream=None):
+        return slim_backward_pairs(self.handle, pts, pose, offsets, vox, gD, gS, self.width,
+                                   stream)
