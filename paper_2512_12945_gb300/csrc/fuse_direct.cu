@@ -10,13 +10,17 @@
 // Blocks: when a ray enters an 8^3 block, the thread looks the block up in
 // the map's hash (the hash table stays in L2), inserting it if it is new
 // (slot from the allocation counter, published with a relaxed store) or
-// waiting (time-bounded) for another thread's publication. The record pool
-// is already zero beyond the counter (see k_zero_used_blocks) and readers
-// use a slot only as the address of their reductions, so a publication
-// orders nothing else and needs no release / acquire pair; the block's key
-// in blk_key is read only by later kernels. A publication needs nothing but
-// its own thread's earlier steps, so no wait can be part of a cycle. (A per-CTA shared-memory cache of block slots in
-// front of the hash was measured slower: 1.81 vs 1.66 ms per 100 scans.)
+// waiting (time-bounded) for another thread's publication. A new block's
+// records are already zero (the pool is zero outside the sub-blocks written
+// since the last reset, see k_zero_touched_blocks) and readers use a slot
+// only as the address of their reductions, so a publication orders nothing
+// else and needs no release / acquire pair; the block's key in blk_key is
+// read only by later kernels. A publication needs nothing but its own
+// thread's earlier steps, so no wait can be part of a cycle. (A per-CTA
+// shared-memory cache of block slots in front of the hash was measured
+// slower: 1.81 vs 1.66 ms per 100 scans.) Each ray marks the 2 x 2 x 2
+// sub-blocks it writes in the block's touched mask (read when it enters the
+// block; reduced into only when a bit is missing) for the reset.
 //
 // One kernel serves a single scan and a batch of scans of many maps (the
 // HashBatch job table): each CTA takes 256 points of one job.

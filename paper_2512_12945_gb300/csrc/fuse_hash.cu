@@ -13,7 +13,8 @@
 //   2. each distinct block of the tile (compacted first) is inserted into
 //      (or found in) the map's hash by its own thread; a block this thread
 //      creates is published at once (its records are already zero: the pool
-//      is kept zero beyond the allocation counter, see k_zero_used_blocks);
+//      is kept zero outside the sub-blocks written since the last reset, see
+//      k_zero_touched_blocks);
 //      only then does the thread wait (time-bounded) for blocks other CTAs
 //      are still publishing, so no wait can be part of a cycle;
 //   3. flush: one vector red.add (S_k += sum d, c_k += count) per table
