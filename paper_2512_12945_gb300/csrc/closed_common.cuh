@@ -25,8 +25,8 @@ __device__ __forceinline__ uint32_t argmax_row(const float* __restrict__ row, in
       float4 v[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        v[q] = (c + q < K4) ? __ldg(r4 + c + q) : make_float4(-INFINITY, -INFINITY, -INFINITY,
-                                                               -INFINITY);
+        v[q] = (c + q < K4) ? __ldcs(r4 + c + q)  // read once: evict first from the caches
+                            : make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const float e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};

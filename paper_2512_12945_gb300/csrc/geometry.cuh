@@ -98,9 +98,11 @@ __device__ __forceinline__ bool ray_setup_at(const ScanGeom& g, const float* __r
     p1 = __fmul_rn(yv, z);
     p2 = z;
   } else {
-    p0 = __ldg(pts + 3 * j);
-    p1 = __ldg(pts + 3 * j + 1);
-    p2 = __ldg(pts + 3 * j + 2);
+    // points are read once per walk: streaming loads, evicted first, so the
+    // map's hash and records keep the caches
+    p0 = __ldcs(pts + 3 * j);
+    p1 = __ldcs(pts + 3 * j + 1);
+    p2 = __ldcs(pts + 3 * j + 2);
   }
   return ray_setup(g, p0, p1, p2, ry);
 }
